@@ -1,0 +1,172 @@
+/*
+ * dyson.h — C ABI of the GB300 lattice Dyson solver.
+ *
+ * Solves the lattice Dyson equation of Dirks, Mikelsons, Krishnamurthy and
+ * Freericks (arXiv:1309.5994), Sec. IV.D, Eqs. (Glatt2) and (Ginvblockstruct),
+ * on the discretised Kadanoff-Baym-Keldysh contour of Sec. IV.A / Fig. 1:
+ *
+ *     G = Lambda + Lambda W J G,
+ *
+ * for a trapped 2D Fermi-Hubbard lattice (Sec. II, Eq. (model)), where
+ * Lambda_i(z,z') is the atomic-limit contour Green's function of site i
+ * (Sec. III; the block-diagonal preconditioner B^-1 of Sec. IV.D with no
+ * self-energy), J_ij(t) the nearest-neighbour hopping (diagonal in contour
+ * time) and W(z) the contour quadrature weights.  The solve runs block column
+ * by block column (one source site, all Nc source times) with the series in
+ * powers of J of App. C, G <- Lambda delta_s + K G.
+ *
+ * Conventions (shared with the CPU oracle, each side implements them itself):
+ *   sites   i = y*Lx + x, open boundaries;
+ *   bonds   horizontal (x,y)-(x+1,y) first, index y*(Lx-1)+x; then vertical
+ *           (x,y)-(x,y+1), index Ly*(Lx-1) + y*Lx + x;  Nb = Ly(Lx-1)+Lx(Ly-1);
+ *   contour Nc = 2*Nt + Nm points in contour order: forward t_k = k*dt
+ *           (index k), backward (index Nt+q carries t_{Nt-1-q}), imaginary
+ *           tau_m = m*beta/Nm (index 2Nt+m); weights +dt, -dt, -i*beta/Nm;
+ *   trap    V_i = curvature * |r_i|^2 about the geometric lattice centre,
+ *           eps_i = V_i - U_i(0)/2 - mu (Eq. (onsitelevels)).
+ *   complex numbers are interleaved (re, im) pairs of doubles.
+ *
+ * Ownership: the context owns every device buffer it allocates (Lambda, its
+ * split-precision copies, hopping tables, observables, work buffers).  The
+ * caller owns every pointer it passes in; none is retained after a call
+ * returns.  All device work is ordered on the stream given to dyson_init.
+ *
+ * Errors: every int-returning call returns DYSON_OK (0) or a negative
+ * DYSON_ERR_* code and never throws; dyson_last_error() describes the last
+ * failure of a context.  No call falls back to a CPU implementation.
+ */
+#ifndef DYSON_H
+#define DYSON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DYSON_OK = 0,
+  DYSON_ERR_INVALID_ARG = -1,   /* a size, pointer or option is out of range            */
+  DYSON_ERR_OOM = -2,           /* device allocation failed                              */
+  DYSON_ERR_NOT_CONVERGED = -3, /* max_sweeps reached above tolerance (results written)  */
+  DYSON_ERR_DIVERGED = -4,      /* update or residual not finite or above 1e200          */
+  DYSON_ERR_TIMEOUT = -5,       /* a bounded device wait expired                          */
+  DYSON_ERR_CUDA = -6,          /* a CUDA runtime call failed                             */
+  DYSON_ERR_STATE = -7          /* call order violated (e.g. solve before build_sigma)    */
+};
+
+/* Arithmetic of the sweeps (App. C series). */
+enum {
+  DYSON_PREC_F64 = 0,           /* complex128 sweeps on the FP64 pipes                   */
+  DYSON_PREC_TF32X3_F64REF = 1  /* complex FP32 sweeps as 3xTF32 tcgen05 products with
+                                   FP32 accumulation, refined by FP64 Dyson residuals     */
+};
+
+typedef struct dyson_ctx dyson_ctx;
+
+typedef struct {
+  int32_t Lx, Ly;               /* lattice sides, >= 1 each, Lx*Ly <= 65535               */
+} dyson_lattice;
+
+typedef struct {
+  int32_t Nt;                   /* real-time points per branch, >= 1                      */
+  int32_t Nm;                   /* imaginary-time points, >= 1; 2*Nt+Nm <= 2048            */
+  double dt;                    /* real-time step, > 0                                    */
+  double beta;                  /* inverse temperature of the initial state, > 0          */
+} dyson_contour;
+
+typedef struct {
+  double curvature;             /* V_trap(r) = curvature * |r|^2                          */
+  double mu;                    /* chemical potential of the initial state                */
+} dyson_trap;
+
+typedef struct {
+  const double* U;              /* host, [Nr][Nt]: U_i(t_k) (U_i(0) also sets eps_i)      */
+  const double* J;              /* host, [Nb][Nt]: J_b(t_k); the imaginary branch uses J_b(0) */
+} dyson_drive;
+
+typedef struct {
+  int32_t sweeps;               /* total series sweeps over all chunks and refinements     */
+  int32_t refinements;          /* FP64 residual evaluations (mixed precision)             */
+  int32_t chunks;               /* column chunks processed                                 */
+  int32_t status;               /* same code the call returned                             */
+  double update;                /* last relative max-norm update of the series             */
+  double residual;              /* last relative max-norm FP64 residual (mixed precision)  */
+  double gemm_flops;            /* algorithmic contour-GEMM flops: 8 Nc^3 per site,
+                                   block column and sweep, over every sweep performed      */
+  double seconds;               /* wall time of the call                                   */
+} dyson_report;
+
+/* Create a context on `device`, ordering work on `cuda_stream` (a cudaStream_t,
+ * NULL for the legacy default stream).  Copies the host drive tables; allocates
+ * Lambda storage (16*Nr*Nc^2 bytes) and small tables.  Sec. II (model),
+ * Sec. IV.A (contour).  Returns INVALID_ARG for out-of-range sizes, OOM if the
+ * device cannot hold Lambda. */
+int dyson_init(dyson_ctx** out, const dyson_lattice* lattice, const dyson_contour* contour,
+               const dyson_trap* trap, const dyson_drive* drive, int device, void* cuda_stream);
+
+/* Build Lambda_i(z,z') of every site in FP64 on the device: Boltzmann weights
+ * of H_0^(i)(0) (Eq. (Z)), the tabulated phases of Eq. (cumulanttabulation)
+ * (left rule dt*sum_{m<k} E(t_m) on the real branches, -i*tau*E(0) on the
+ * imaginary one) and the closed form of the two transition channels (Sec. III).
+ * Equal contour points are 'lesser' on the forward and imaginary branches and
+ * 'greater' on the backward branch. */
+int dyson_build_sigma(dyson_ctx* ctx);
+
+/* Copy Lambda, [Nr][Nc][Nc] complex128 (row z, column z'), into dst (caller
+ * owned, 16*Nr*Nc*Nc bytes; device memory if on_device != 0, else host).
+ * Returns STATE before dyson_build_sigma. */
+int dyson_copy_sigma(dyson_ctx* ctx, double* dst, int on_device);
+
+/* Solve block columns G(:, s) for the n_src source sites src_sites (host array,
+ * each in [0, Nr), repeats allowed) with the App. C series, to a relative
+ * max-norm update (F64) or FP64 residual (mixed precision) <= tol, relative to
+ * max|Lambda_s|, within max_sweeps series sweeps per solve.  Columns are
+ * processed in chunks sized to the free device memory.
+ *   g_out: NULL, or a caller-owned DEVICE buffer of n_src*Nr*Nc*Nc complex128
+ *          receiving G_js(z, z') at [q][j][z][z'] for source src_sites[q].
+ * Observables of every source site are computed as a side effect (see
+ * dyson_observables).  rep may be NULL. */
+int dyson_solve_columns(dyson_ctx* ctx, const int32_t* src_sites, int64_t n_src, int precision,
+                        double tol, int32_t max_sweeps, double* g_out, dyson_report* rep);
+
+/* Observables of the sites solved so far (Sec. III.A, Eq. (docc), App. B):
+ * density per spin n_i(t_k), kinetic energy ekin_i(t_k) and double occupancy
+ * D_i(t_k), each [Nr][Nt] doubles.  Sites never solved hold NaN; D_i(t_0) is
+ * NaN (the difference quotient needs t_{k-1}).  The kinetic energy is
+ * Re[-i sum_j J_ij G_ji(t,t)]: the solved G is that of hopping +J, the gauge
+ * image of Eq. (model) on the bipartite lattice.  Each pointer may be NULL;
+ * on_device != 0 means the pointers are device memory, else host memory. */
+int dyson_observables(dyson_ctx* ctx, double* n, double* ekin, double* docc, int on_device);
+
+void dyson_destroy(dyson_ctx* ctx);
+const char* dyson_last_error(const dyson_ctx* ctx);
+
+/* Kernel kinds timed by the optional per-launch CUDA-event profiler. */
+enum {
+  DYSON_KERNEL_SWEEP_F64 = 0,     /* FP64 series sweep (gather + complex GEMM)               */
+  DYSON_KERNEL_SWEEP_F32 = 1,     /* FP32 CUDA-core sweep                                    */
+  DYSON_KERNEL_SWEEP_TC = 2,      /* 3xTF32 tcgen05 sweep (gather + split + GEMM)            */
+  DYSON_KERNEL_RESIDUAL_F64 = 3,  /* FP64 Dyson residual r = Lambda delta + K G - G          */
+  DYSON_KERNEL_KINDS = 4
+};
+
+/* Enable (1) or disable (0) event timing of every sweep/residual launch on the
+ * context's stream and reset the counters.  Timing adds two events per launch. */
+int dyson_profile(dyson_ctx* ctx, int enable);
+
+/* Launch count and summed device time (ms) of one DYSON_KERNEL_* kind since
+ * the last dyson_profile call. */
+int dyson_profile_query(dyson_ctx* ctx, int kind, int64_t* launches, double* total_ms);
+
+/* Cap the number of block columns solved together (0 = size from free memory). */
+int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);
+
+/* Library version string. */
+const char* dyson_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DYSON_H */

@@ -1,0 +1,186 @@
+"""ctypes binding of libdyson.so (the C ABI of include/dyson.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Loading fails with an exception when the library has not been built;
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libdyson.so")
+_lib = None
+
+DYSON_OK = 0
+ERR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_CONVERGED", -4: "DIVERGED", -5: "TIMEOUT",
+             -6: "CUDA", -7: "STATE"}
+PREC_F64 = 0
+PREC_TF32X3_F64REF = 1
+KERNEL_SWEEP_F64, KERNEL_SWEEP_F32, KERNEL_SWEEP_TC, KERNEL_RESIDUAL_F64 = 0, 1, 2, 3
+KERNEL_NAMES = {0: "sweep_f64", 1: "sweep_f32_simt", 2: "sweep_tc_3xtf32", 3: "residual_f64"}
+
+
+class Lattice(C.Structure):
+    _fields_ = [("Lx", C.c_int32), ("Ly", C.c_int32)]
+
+
+class Contour(C.Structure):
+    _fields_ = [("Nt", C.c_int32), ("Nm", C.c_int32), ("dt", C.c_double), ("beta", C.c_double)]
+
+
+class Trap(C.Structure):
+    _fields_ = [("curvature", C.c_double), ("mu", C.c_double)]
+
+
+class Drive(C.Structure):
+    _fields_ = [("U", C.POINTER(C.c_double)), ("J", C.POINTER(C.c_double))]
+
+
+class Report(C.Structure):
+    _fields_ = [("sweeps", C.c_int32), ("refinements", C.c_int32), ("chunks", C.c_int32),
+                ("status", C.c_int32), ("update", C.c_double), ("residual", C.c_double),
+                ("gemm_flops", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_columns",
+           "dyson_observables", "dyson_profile", "dyson_profile_query", "dyson_set_chunk",
+           "dyson_destroy", "dyson_last_error", "dyson_version"]
+
+
+def load(path: str = _LIB_PATH):
+    """Load libdyson.so and declare the signatures of include/dyson.h."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    lib.dyson_init.argtypes = [C.POINTER(P), C.POINTER(Lattice), C.POINTER(Contour), C.POINTER(Trap),
+                               C.POINTER(Drive), C.c_int, P]
+    lib.dyson_build_sigma.argtypes = [P]
+    lib.dyson_copy_sigma.argtypes = [P, P, C.c_int]
+    lib.dyson_solve_columns.argtypes = [P, C.POINTER(C.c_int32), C.c_int64, C.c_int, C.c_double, C.c_int32, P,
+                                        C.POINTER(Report)]
+    lib.dyson_observables.argtypes = [P, P, P, P, C.c_int]
+    lib.dyson_profile.argtypes = [P, C.c_int]
+    lib.dyson_profile_query.argtypes = [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+    lib.dyson_set_chunk.argtypes = [P, C.c_int32]
+    lib.dyson_destroy.argtypes = [P]
+    lib.dyson_destroy.restype = None
+    lib.dyson_last_error.argtypes = [P]
+    lib.dyson_last_error.restype = C.c_char_p
+    lib.dyson_version.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class DysonError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+@dataclass
+class SolveResult:
+    status: int
+    report: dict
+
+
+class Solver:
+    """One context of the C ABI for a workloads.Problem-like object.
+
+    `stream` is a torch.cuda.Stream (or None for torch's current stream).
+    """
+
+    def __init__(self, problem, device: int = 0, stream=None):
+        import torch
+        self.lib = load()
+        self.p = problem
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self._U = np.ascontiguousarray(problem.U, dtype=np.float64)
+        self._J = np.ascontiguousarray(problem.J, dtype=np.float64)
+        lat = Lattice(problem.Lx, problem.Ly)
+        con = Contour(problem.Nt, problem.Nm, problem.dt, problem.beta)
+        trap = Trap(problem.trap_c, problem.mu)
+        drv = Drive(self._U.ctypes.data_as(C.POINTER(C.c_double)), self._J.ctypes.data_as(C.POINTER(C.c_double)))
+        h = C.c_void_p()
+        rc = self.lib.dyson_init(C.byref(h), C.byref(lat), C.byref(con), C.byref(trap), C.byref(drv), device,
+                                 C.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise DysonError(rc, self.lib.dyson_last_error(None).decode())
+        self.h = h
+        self.device = device
+
+    def _check(self, rc, ok=(0,)):
+        if rc not in ok:
+            raise DysonError(rc, self.lib.dyson_last_error(self.h).decode())
+        return rc
+
+    def build_sigma(self):
+        self._check(self.lib.dyson_build_sigma(self.h))
+
+    def sigma(self):
+        """Lambda as a host complex128 array [Nr, Nc, Nc]."""
+        out = np.empty((self.p.Nr, self.p.Nc, self.p.Nc), dtype=np.complex128)
+        self._check(self.lib.dyson_copy_sigma(self.h, out.ctypes.data, 0))
+        return out
+
+    def solve(self, sources, precision=PREC_F64, tol=1e-13, max_sweeps=400, g_out=None, allow=(0,)):
+        """Solve block columns for `sources`; g_out: optional complex128 device tensor
+        of shape [len(sources), Nr, Nc, Nc].  Returns SolveResult."""
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+        rep = Report()
+        gptr = None
+        if g_out is not None:
+            assert g_out.is_cuda and g_out.dtype == self._torch.complex128 and g_out.is_contiguous()
+            assert g_out.numel() == len(src) * self.p.Nr * self.p.Nc * self.p.Nc
+            gptr = C.c_void_p(g_out.data_ptr())
+        rc = self.lib.dyson_solve_columns(self.h, src.ctypes.data_as(C.POINTER(C.c_int32)), len(src), precision,
+                                          tol, max_sweeps, gptr, C.byref(rep))
+        self._check(rc, ok=allow)
+        return SolveResult(rc, rep.as_dict())
+
+    def observables(self):
+        """(n, ekin, D) as host numpy arrays [Nr, Nt]."""
+        shape = (self.p.Nr, self.p.Nt)
+        n, e, d = (np.empty(shape) for _ in range(3))
+        self._check(self.lib.dyson_observables(self.h, n.ctypes.data, e.ctypes.data, d.ctypes.data, 0))
+        return n, e, d
+
+    def observables_device(self, n, ekin, docc):
+        self._check(self.lib.dyson_observables(self.h, C.c_void_p(n.data_ptr()), C.c_void_p(ekin.data_ptr()),
+                                               C.c_void_p(docc.data_ptr()), 1))
+
+    def set_chunk(self, cols: int):
+        self._check(self.lib.dyson_set_chunk(self.h, cols))
+
+    def profile(self, enable: bool):
+        self._check(self.lib.dyson_profile(self.h, 1 if enable else 0))
+
+    def profile_query(self, kind: int):
+        n = C.c_int64()
+        ms = C.c_double()
+        self._check(self.lib.dyson_profile_query(self.h, kind, C.byref(n), C.byref(ms)))
+        return n.value, ms.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dyson_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,513 @@
+// Entry points of the C ABI declared in include/dyson.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <limits>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace {
+
+thread_local std::string g_noctx_err;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int fail_noctx(int code, const std::string& m) {
+  g_noctx_err = m;
+  return code;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+double bits_to_double(unsigned long long b) {
+  double d;
+  std::memcpy(&d, &b, sizeof d);
+  return d;
+}
+
+// -------------------------------------------------------------------------
+// per-kernel-kind timing with events on the library stream
+// -------------------------------------------------------------------------
+struct KernelTimer {
+  dyson_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KernelTimer(dyson_ctx* cc, int k) : c(cc), kind(k) {
+    if (!c->profiling) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->stream);
+  }
+  ~KernelTimer() {
+    if (!a) return;
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({kind, a, b});
+  }
+};
+
+void flush_timers(dyson_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->prof_ms[p.kind] += ms;
+      c->prof_launches[p.kind] += 1;
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  c->pending.clear();
+}
+
+int ensure_work(dyson_ctx* c, size_t bytes) {
+  if (c->work_bytes >= bytes) return DYSON_OK;
+  if (c->work) cudaFree(c->work);
+  c->work = nullptr;
+  c->work_bytes = 0;
+  cudaError_t e = cudaMalloc(&c->work, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, DYSON_ERR_OOM, "work buffer of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  }
+  c->work_bytes = bytes;
+  return DYSON_OK;
+}
+
+int ensure_cols(dyson_ctx* c, int nq) {
+  if (c->col_src_cap < nq) {
+    if (c->d_col_src) cudaFree(c->d_col_src);
+    c->d_col_src = nullptr;
+    DY_CUDA(c, dalloc(&c->d_col_src, nq));
+    c->col_src_cap = nq;
+  }
+  if (c->norm_cap < nq) {
+    if (c->d_norm) cudaFree(c->d_norm);
+    if (c->h_norm) cudaFreeHost(c->h_norm);
+    c->d_norm = nullptr;
+    c->h_norm = nullptr;
+    DY_CUDA(c, dalloc(&c->d_norm, 2 * (size_t)nq));
+    DY_CUDA(c, cudaMallocHost((void**)&c->h_norm, 2 * (size_t)nq * sizeof(unsigned long long)));
+    c->norm_cap = nq;
+  }
+  return DYSON_OK;
+}
+
+// read norm[0..nq) (and scale[nq..2nq) when with_scale) to the host
+int read_norms(dyson_ctx* c, int nq, bool with_scale) {
+  DY_CUDA(c, cudaMemcpyAsync(c->h_norm, c->d_norm, (with_scale ? 2 : 1) * (size_t)nq * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  flush_timers(c);
+  return DYSON_OK;
+}
+
+// max over block columns of norm[q] / ref[q]
+double rel_max(const unsigned long long* norm, const double* ref, int nq) {
+  double m = 0.0;
+  for (int q = 0; q < nq; ++q) {
+    double v = bits_to_double(norm[q]) / std::max(ref[q], 1e-300);
+    if (!(v == v)) return std::numeric_limits<double>::infinity();
+    m = std::max(m, v);
+  }
+  return m;
+}
+
+constexpr double kDivergedGrowth = 1e200;
+
+// plain FP64 series: G <- B + K G until the relative update <= tol
+int solve_f64(dyson_ctx* c, int nq, double tol, int max_sweeps, double2** result, dyson_report* r) {
+  const size_t ncol = (size_t)nq * c->Nc, n_el = (size_t)c->Nr * ncol * c->Nc;
+  double2* Ga = (double2*)c->work;
+  double2* Gb = Ga + n_el;
+  DY_CUDA(c, cudaMemsetAsync(Ga, 0, n_el * sizeof(double2), c->stream));
+  DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, 2 * (size_t)nq * sizeof(unsigned long long), c->stream));
+  launch_init_rhs(c->d_lam, c->d_col_src, c->Nr, c->Nc, (int)ncol, Ga, c->d_norm + nq, c->stream);
+  int rc = read_norms(c, nq, true);
+  if (rc) return rc;
+  std::vector<double> scale(nq);
+  for (int q = 0; q < nq; ++q) scale[q] = bits_to_double(c->h_norm[nq + q]);
+  int status = DYSON_ERR_NOT_CONVERGED;
+  for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
+    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)nq * sizeof(unsigned long long), c->stream));
+    {
+      KernelTimer t(c, DYSON_KERNEL_SWEEP_F64);
+      launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, Ga, Gb, nullptr, c->d_col_src, c->Nr, c->Nc,
+                       (int)ncol, 0, c->d_norm, c->stream);
+    }
+    DY_CUDA(c, cudaGetLastError());
+    if ((rc = read_norms(c, nq, false))) return rc;
+    std::swap(Ga, Gb);
+    double upd = rel_max(c->h_norm, scale.data(), nq);
+    r->sweeps += 1;
+    r->gemm_flops += 8.0 * c->Nc * (double)c->Nc * c->Nc * c->Nr * nq;
+    r->update = upd;
+    if (!(upd < kDivergedGrowth)) {
+      status = DYSON_ERR_DIVERGED;
+      break;
+    }
+    if (upd <= tol) {
+      status = DYSON_OK;
+      break;
+    }
+  }
+  *result = Ga;
+  return status;
+}
+
+// inner solve d <- r + K d in FP32 (SIMT or 3xTF32 tensor cores)
+int inner_solve(dyson_ctx* c, int nq, int precision, float* r32, float* da, float* db, int max_sweeps,
+                const std::vector<double>& rref, float** dres, dyson_report* rep) {
+  const size_t ncol = (size_t)nq * c->Nc, n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
+  DY_CUDA(c, cudaMemcpyAsync(da, r32, n32 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  double best = std::numeric_limits<double>::infinity(), peak = 0.0;
+  int since_best = 0, rc;
+  for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
+    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)nq * sizeof(unsigned long long), c->stream));
+    if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
+      KernelTimer t(c, DYSON_KERNEL_SWEEP_TC);
+      if ((rc = tc_sweep(c, nq, r32, da, db))) return rc;
+    } else {
+      KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
+      launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, (int)ncol,
+                            c->d_norm, c->stream);
+    }
+    DY_CUDA(c, cudaGetLastError());
+    if ((rc = read_norms(c, nq, false))) return rc;
+    if (c->use_tc && (rc = tc_check_error(c))) return rc;
+    std::swap(da, db);
+    double upd = rel_max(c->h_norm, rref.data(), nq);
+    rep->sweeps += 1;
+    rep->gemm_flops += 8.0 * c->Nc * (double)c->Nc * c->Nc * c->Nr * nq;
+    rep->update = upd;
+    if (!(upd < kDivergedGrowth)) return ctx_fail(c, DYSON_ERR_DIVERGED, "FP32 series update not finite");
+    // The update first grows (transient of the real-time series), falls
+    // factorially after its peak, then settles at the FP32 rounding level of the
+    // partial sums.  Stop at 4e-7, or once it sits 1e-4 below its peak and has
+    // not improved for 4 sweeps.
+    peak = std::max(peak, upd);
+    if (upd < best) {
+      best = upd;
+      since_best = 0;
+    } else {
+      ++since_best;
+    }
+    if (upd <= 4e-7) break;
+    if (since_best >= 4 && best < 1e-4 * peak) break;
+  }
+  *dres = da;
+  return DYSON_OK;
+}
+
+// complex FP32 series refined by FP64 residuals: G += solve(r), r = B + K G - G
+int solve_mixed(dyson_ctx* c, int nq, int precision, double tol, int max_sweeps, double2** result,
+                dyson_report* rep) {
+  const size_t ncol = (size_t)nq * c->Nc, n_el = (size_t)c->Nr * ncol * c->Nc;
+  double2* G = (double2*)c->work;
+  float* r32 = (float*)(G + n_el);
+  float* da = r32 + 2 * n_el;
+  float* db = da + 2 * n_el;
+  int rc;
+  // r = B (FP32), scale = max |Lambda_s|; G = 0
+  DY_CUDA(c, cudaMemsetAsync(G, 0, n_el * sizeof(double2), c->stream));
+  DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, 2 * (size_t)nq * sizeof(unsigned long long), c->stream));
+  launch_init_rhs(c->d_lam, c->d_col_src, c->Nr, c->Nc, (int)ncol, G, c->d_norm + nq, c->stream);
+  launch_to_planar32(G, r32, n_el, c->Nc, c->stream);
+  DY_CUDA(c, cudaMemsetAsync(G, 0, n_el * sizeof(double2), c->stream));
+  if ((rc = read_norms(c, nq, true))) return rc;
+  std::vector<double> scale(nq), rref(nq);
+  for (int q = 0; q < nq; ++q) rref[q] = scale[q] = bits_to_double(c->h_norm[nq + q]);
+  int status = DYSON_ERR_NOT_CONVERGED;
+  for (int ref = 0; ref < c->max_refinements; ++ref) {
+    float* d = nullptr;
+    if ((rc = inner_solve(c, nq, precision, r32, da, db, max_sweeps, rref, &d, rep))) return rc;
+    launch_accumulate(G, d, c->Nr, c->Nc, (int)ncol, c->stream);
+    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)nq * sizeof(unsigned long long), c->stream));
+    {
+      KernelTimer t(c, DYSON_KERNEL_RESIDUAL_F64);
+      launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, G, nullptr, r32, c->d_col_src, c->Nr, c->Nc,
+                       (int)ncol, 1, c->d_norm, c->stream);
+    }
+    DY_CUDA(c, cudaGetLastError());
+    if ((rc = read_norms(c, nq, false))) return rc;
+    rep->refinements += 1;
+    rep->gemm_flops += 8.0 * c->Nc * (double)c->Nc * c->Nc * c->Nr * nq;
+    double res = rel_max(c->h_norm, scale.data(), nq);
+    rep->residual = res;
+    for (int q = 0; q < nq; ++q) rref[q] = std::max(bits_to_double(c->h_norm[q]), 1e-300);
+    if (!(res < kDivergedGrowth)) {
+      status = DYSON_ERR_DIVERGED;
+      break;
+    }
+    if (res <= tol) {
+      status = DYSON_OK;
+      break;
+    }
+  }
+  *result = G;
+  return status;
+}
+
+}  // namespace
+
+int ctx_fail(dyson_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_noctx_err = msg;
+  return code;
+}
+
+extern "C" {
+
+const char* dyson_version(void) { return "gb300-dyson 0.1 (sm_103a)"; }
+
+const char* dyson_last_error(const dyson_ctx* ctx) { return ctx ? ctx->err.c_str() : g_noctx_err.c_str(); }
+
+int dyson_init(dyson_ctx** out, const dyson_lattice* L, const dyson_contour* C, const dyson_trap* T,
+               const dyson_drive* D, int device, void* stream) {
+  if (!out) return fail_noctx(DYSON_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!L || !C || !T || !D || !D->U || !D->J) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL argument");
+  if (L->Lx < 1 || L->Ly < 1 || (int64_t)L->Lx * L->Ly > 65535)
+    return fail_noctx(DYSON_ERR_INVALID_ARG, "lattice must have 1..65535 sites");
+  if (C->Nt < 1 || C->Nm < 1 || 2 * (int64_t)C->Nt + C->Nm > 2048)
+    return fail_noctx(DYSON_ERR_INVALID_ARG, "need Nt >= 1, Nm >= 1 and 2*Nt+Nm <= 2048");
+  if (!(C->dt > 0) || !(C->beta > 0) || !std::isfinite(C->dt) || !std::isfinite(C->beta))
+    return fail_noctx(DYSON_ERR_INVALID_ARG, "dt and beta must be positive and finite");
+  if (!std::isfinite(T->curvature) || !std::isfinite(T->mu))
+    return fail_noctx(DYSON_ERR_INVALID_ARG, "trap parameters must be finite");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return fail_noctx(DYSON_ERR_INVALID_ARG, "no such CUDA device");
+  DeviceGuard g(device);
+  auto* c = new dyson_ctx;
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  c->Lx = L->Lx;
+  c->Ly = L->Ly;
+  c->Nr = L->Lx * L->Ly;
+  c->Nb = L->Ly * (L->Lx - 1) + L->Lx * (L->Ly - 1);
+  c->Nt = C->Nt;
+  c->Nm = C->Nm;
+  c->Nc = 2 * C->Nt + C->Nm;
+  c->dt = C->dt;
+  c->beta = C->beta;
+  c->curvature = T->curvature;
+  c->mu = T->mu;
+  c->U.assign(D->U, D->U + (size_t)c->Nr * c->Nt);
+  c->J.assign(D->J, D->J + (size_t)c->Nb * c->Nt);
+  for (double v : c->U)
+    if (!std::isfinite(v)) {
+      delete c;
+      return fail_noctx(DYSON_ERR_INVALID_ARG, "U table holds a non-finite value");
+    }
+  for (double v : c->J)
+    if (!std::isfinite(v)) {
+      delete c;
+      return fail_noctx(DYSON_ERR_INVALID_ARG, "J table holds a non-finite value");
+    }
+  if (const char* e = std::getenv("DYSON_MAX_REFINEMENTS")) c->max_refinements = std::max(1, atoi(e));
+  if (const char* e = std::getenv("DYSON_NO_TC")) c->tc_enabled = !(e[0] == '1');
+
+  // neighbour slots (+x, -x, +y, -y) with their bond indices
+  std::vector<int> nbr((size_t)c->Nr * 4, -1), nbond((size_t)c->Nr * 4, -1);
+  for (int y = 0; y < c->Ly; ++y)
+    for (int x = 0; x < c->Lx; ++x) {
+      int i = y * c->Lx + x;
+      if (x + 1 < c->Lx) { nbr[i * 4 + 0] = i + 1; nbond[i * 4 + 0] = y * (c->Lx - 1) + x; }
+      if (x > 0) { nbr[i * 4 + 1] = i - 1; nbond[i * 4 + 1] = y * (c->Lx - 1) + x - 1; }
+      int vb = c->Ly * (c->Lx - 1);
+      if (y + 1 < c->Ly) { nbr[i * 4 + 2] = i + c->Lx; nbond[i * 4 + 2] = vb + y * c->Lx + x; }
+      if (y > 0) { nbr[i * 4 + 3] = i - c->Lx; nbond[i * 4 + 3] = vb + (y - 1) * c->Lx + x; }
+    }
+  const size_t NcNc = (size_t)c->Nc * c->Nc;
+  auto bail = [&](cudaError_t e, const char* what) {
+    int code = e == cudaErrorMemoryAllocation ? DYSON_ERR_OOM : DYSON_ERR_CUDA;
+    cudaGetLastError();
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    dyson_destroy(c);
+    return fail_noctx(code, m);
+  };
+  cudaError_t e;
+  if ((e = dalloc(&c->dU, c->U.size())) || (e = dalloc(&c->dJ, c->J.size())) ||
+      (e = dalloc(&c->d_nbr, nbr.size())) || (e = dalloc(&c->d_nbond, nbond.size())) ||
+      (e = dalloc(&c->d_eps, (size_t)c->Nr)) || (e = dalloc(&c->d_phase, (size_t)c->Nr * (2 * c->Nc + 2))) ||
+      (e = dalloc(&c->d_lam, (size_t)c->Nr * NcNc)) || (e = dalloc(&c->d_JW, (size_t)c->Nb * c->Nc)) ||
+      (e = dalloc(&c->d_Jz, (size_t)c->Nb * c->Nc)) || (e = dalloc(&c->d_obs, 3 * (size_t)c->Nr * c->Nt)))
+    return bail(e, "device allocation");
+  std::vector<double> nan_obs(3 * (size_t)c->Nr * c->Nt, std::numeric_limits<double>::quiet_NaN());
+  if ((e = cudaMemcpyAsync(c->dU, c->U.data(), c->U.size() * 8, cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaMemcpyAsync(c->dJ, c->J.data(), c->J.size() * 8, cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaMemcpyAsync(c->d_nbr, nbr.data(), nbr.size() * 4, cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaMemcpyAsync(c->d_nbond, nbond.data(), nbond.size() * 4, cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaMemcpyAsync(c->d_obs, nan_obs.data(), nan_obs.size() * 8, cudaMemcpyHostToDevice, c->stream)) ||
+      (e = cudaStreamSynchronize(c->stream)))
+    return bail(e, "table upload");
+  *out = c;
+  return DYSON_OK;
+}
+
+int dyson_build_sigma(dyson_ctx* c) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  DeviceGuard g(c->device);
+  launch_build_sigma(c->dU, c->Lx, c->Ly, c->Nt, c->Nm, c->dt, c->beta, c->curvature, c->mu, c->d_eps,
+                     c->d_phase, c->d_lam, c->stream);
+  launch_hopping_tables(c->dJ, c->Nb, c->Nt, c->Nm, c->dt, c->beta, c->d_JW, c->d_Jz, c->stream);
+  DY_CUDA(c, cudaGetLastError());
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->sigma_built = true;
+  c->lam32_built = c->lam_split_built = false;
+  return DYSON_OK;
+}
+
+int dyson_copy_sigma(dyson_ctx* c, double* dst, int on_device) {
+  if (!c || !dst) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL argument");
+  if (!c->sigma_built) return ctx_fail(c, DYSON_ERR_STATE, "dyson_build_sigma has not run");
+  DeviceGuard g(c->device);
+  DY_CUDA(c, cudaMemcpyAsync(dst, c->d_lam, (size_t)c->Nr * c->Nc * c->Nc * sizeof(double2),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DYSON_OK;
+}
+
+int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
+                        int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  dyson_report rep;
+  std::memset(&rep, 0, sizeof rep);
+  auto t0 = std::chrono::steady_clock::now();
+  auto finish = [&](int code) {
+    rep.status = code;
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep_out) *rep_out = rep;
+    return code;
+  };
+  if (!c->sigma_built) return finish(ctx_fail(c, DYSON_ERR_STATE, "dyson_build_sigma has not run"));
+  if (n_src < 1 || !src) return finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "need at least one source site"));
+  for (int64_t q = 0; q < n_src; ++q)
+    if (src[q] < 0 || src[q] >= c->Nr) return finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "source site out of range"));
+  if (precision != DYSON_PREC_F64 && precision != DYSON_PREC_TF32X3_F64REF)
+    return finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "unknown precision"));
+  if (!(tol > 0) || max_sweeps < 1) return finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "need tol > 0 and max_sweeps >= 1"));
+  DeviceGuard g(c->device);
+  int rc;
+  if (precision != DYSON_PREC_F64) {
+    if (!c->lam32_built && (!c->tc_enabled || !tc_supported(c, c->Nc))) {
+      if (!c->d_lam32) DY_CUDA(c, dalloc(&c->d_lam32, (size_t)c->Nr * c->Nc * c->Nc));
+      launch_lam_c64(c->d_lam, c->Nr, c->Nt, c->Nm, c->dt, c->beta, c->d_lam32, c->stream);
+      c->lam32_built = true;
+    }
+    if (c->tc_enabled && tc_supported(c, c->Nc) && !c->lam_split_built) {
+      size_t n = (size_t)c->Nr * 4 * c->Nc * c->Nc;
+      if (!c->d_lam_hi) DY_CUDA(c, dalloc(&c->d_lam_hi, n));
+      if (!c->d_lam_lo) DY_CUDA(c, dalloc(&c->d_lam_lo, n));
+      launch_lam_emb_split(c->d_lam, c->Nr, c->Nt, c->Nm, c->dt, c->beta, c->d_lam_hi, c->d_lam_lo, c->stream);
+      c->lam_split_built = true;
+    }
+    c->use_tc = c->tc_enabled && tc_supported(c, c->Nc);
+    if (!c->use_tc && !c->lam32_built) return finish(ctx_fail(c, DYSON_ERR_STATE, "FP32 tables missing"));
+  }
+  // chunk size from free device memory (bytes per block column of work state)
+  // F64: two complex128 states; mixed: complex128 G + three FP32 states (+ the
+  // FP32 gather buffer of the tensor-core sweep)
+  const double per_el = precision == DYSON_PREC_F64 ? 32.0 : (c->use_tc ? 48.0 : 40.0);
+  const double col_bytes = per_el * c->Nr * (double)c->Nc * c->Nc;
+  size_t free_b = 0, total_b = 0;
+  DY_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
+  double budget = 0.85 * (double)(free_b + c->work_bytes);
+  int64_t chunk = (int64_t)(budget / col_bytes);
+  if (const char* e = std::getenv("DYSON_CHUNK")) chunk = std::min<int64_t>(chunk, std::max(1, atoi(e)));
+  if (c->chunk_override > 0) chunk = std::min<int64_t>(chunk, c->chunk_override);
+  chunk = std::min<int64_t>(std::min<int64_t>(chunk, n_src), 65535);
+  if (chunk < 1) return finish(ctx_fail(c, DYSON_ERR_OOM, "one block column does not fit in device memory"));
+  if ((rc = ensure_work(c, (size_t)(chunk * col_bytes)))) return finish(rc);
+  if ((rc = ensure_cols(c, (int)chunk))) return finish(rc);
+
+  int status = DYSON_OK;
+  for (int64_t start = 0; start < n_src; start += chunk) {
+    int nq = (int)std::min<int64_t>(chunk, n_src - start);
+    size_t ncol = (size_t)nq * c->Nc;
+    DY_CUDA(c, cudaMemcpyAsync(c->d_col_src, src + start, nq * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    double2* G = nullptr;
+    int st = precision == DYSON_PREC_F64 ? solve_f64(c, nq, tol, max_sweeps, &G, &rep)
+                                         : solve_mixed(c, nq, precision, tol, max_sweeps, &G, &rep);
+    if (st != DYSON_OK && st != DYSON_ERR_NOT_CONVERGED && st != DYSON_ERR_DIVERGED) return finish(st);
+    if (st != DYSON_OK && status == DYSON_OK) status = st;
+    rep.chunks += 1;
+    launch_observables(G, c->d_col_src, nq, c->d_nbr, c->d_nbond, c->dJ, c->d_eps, c->dU, c->Nr, c->Nt, c->Nc,
+                       (int)ncol, c->dt, c->d_obs, c->stream);
+    if (g_out) launch_export(G, c->Nr, c->Nc, nq, (double2*)g_out + (size_t)start * c->Nr * c->Nc * c->Nc, c->stream);
+    DY_CUDA(c, cudaGetLastError());
+  }
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  flush_timers(c);
+  if (status == DYSON_ERR_NOT_CONVERGED) ctx_fail(c, status, "max_sweeps or refinement limit reached above tolerance");
+  if (status == DYSON_ERR_DIVERGED) ctx_fail(c, status, "series diverged (update not finite or above 1e200)");
+  return finish(status);
+}
+
+int dyson_observables(dyson_ctx* c, double* n, double* ekin, double* docc, int on_device) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  DeviceGuard g(c->device);
+  size_t cnt = (size_t)c->Nr * c->Nt;
+  double* dst[3] = {n, ekin, docc};
+  for (int k = 0; k < 3; ++k)
+    if (dst[k])
+      DY_CUDA(c, cudaMemcpyAsync(dst[k], c->d_obs + k * cnt, cnt * sizeof(double),
+                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DYSON_OK;
+}
+
+int dyson_profile(dyson_ctx* c, int enable) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  flush_timers(c);
+  c->profiling = enable != 0;
+  for (int k = 0; k < DYSON_KERNEL_KINDS; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_launches[k] = 0;
+  }
+  return DYSON_OK;
+}
+
+int dyson_profile_query(dyson_ctx* c, int kind, int64_t* launches, double* total_ms) {
+  if (!c || kind < 0 || kind >= DYSON_KERNEL_KINDS) return fail_noctx(DYSON_ERR_INVALID_ARG, "bad kernel kind");
+  flush_timers(c);
+  if (launches) *launches = c->prof_launches[kind];
+  if (total_ms) *total_ms = c->prof_ms[kind];
+  return DYSON_OK;
+}
+
+int dyson_set_chunk(dyson_ctx* c, int32_t block_columns) {
+  if (!c || block_columns < 0) return fail_noctx(DYSON_ERR_INVALID_ARG, "bad chunk size");
+  c->chunk_override = block_columns;
+  return DYSON_OK;
+}
+
+void dyson_destroy(dyson_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  flush_timers(c);
+  tc_release(c);
+  void* ptrs[] = {c->dU, c->dJ, c->d_nbr, c->d_nbond, c->d_eps, c->d_phase, c->d_lam, c->d_JW, c->d_Jz,
+                  c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_col_src, c->d_norm};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_norm) cudaFreeHost(c->h_norm);
+  delete c;
+}
+
+}  // extern "C"

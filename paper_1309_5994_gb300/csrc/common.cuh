@@ -1,0 +1,134 @@
+// Internal declarations shared by the translation units of the Dyson library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dyson.h"
+
+// ---------------------------------------------------------------------------
+// device helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// max of non-negative doubles through their ordered bit patterns
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double v) {
+  if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000ULL);  // NaN -> +inf: never converges
+  atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// kernel launchers (all asynchronous on `s`)
+// ---------------------------------------------------------------------------
+
+// K1: atomic-limit functions.  eps [Nr], Lam [Nr][Nc][Nc] complex128.
+void launch_build_sigma(const double* U, int Lx, int Ly, int Nt, int Nm, double dt, double beta,
+                        double curvature, double mu, double* eps, double2* phase,
+                        double2* lam, cudaStream_t s);
+// contour hopping weights JW[b][z] = W(z) J_b(t(z)) (complex128) and Jz[b][z] = J_b(t(z)) (fp32)
+void launch_hopping_tables(const double* J, int Nb, int Nt, int Nm, double dt, double beta,
+                           double2* JW, float* Jz, cudaStream_t s);
+// Lambda' = Lambda * W as complex64 (SIMT FP32 path)
+void launch_lam_c64(const double2* lam, int Nr, int Nt, int Nm, double dt, double beta,
+                    float2* lam32, cudaStream_t s);
+// Lambda' = Lambda * W as the real 2Nc x 2Nc embedding [[Re,-Im],[Im,Re]], split in
+// TF32 hi + lo parts (tcgen05 path).  hi/lo: [Nr][2Nc][2Nc] fp32.
+void launch_lam_emb_split(const double2* lam, int Nr, int Nt, int Nm, double dt, double beta,
+                          float* hi, float* lo, cudaStream_t s);
+
+// chunk state: FP64 state [Nr][ncol][Nc] complex128, FP32 state [Nr][ncol][2Nc] planar
+void launch_init_rhs(const double2* lam, const int* col_src, int Nr, int Nc, int ncol, double2* G,
+                     unsigned long long* scale, cudaStream_t s);
+// K3: out = B + K Gin (mode 0), or B + K Gin - Gin (mode 1); norm[q] = max |out - Gin| (mode 0)
+// or max |out| (mode 1).  If out32 != nullptr (mode 1 only) the result is written as FP32
+// planar state instead of into out.
+void launch_sweep_f64(const double2* lam, const double2* JW, const int* nbr, const int* nbond,
+                      const double2* Gin, double2* out, float* out32, const int* col_src, int Nr,
+                      int Nc, int ncol, int mode, unsigned long long* norm, cudaStream_t s);
+// SIMT FP32 sweep: dout = r + K din over planar FP32 state; norm[q] = max |dout - din|
+void launch_sweep_f32_simt(const float2* lam32, const float* Jz, const int* nbr, const int* nbond,
+                           const float* r, const float* din, float* dout, int Nr, int Nc, int ncol,
+                           unsigned long long* norm, cudaStream_t s);
+// FP64 interleaved state -> FP32 planar state
+void launch_to_planar32(const double2* G, float* out, size_t n_el, int Nc, cudaStream_t s);
+// G64 += d32
+void launch_accumulate(double2* G, const float* d, int Nr, int Nc, int ncol, cudaStream_t s);
+// observables of the block columns of a chunk
+void launch_observables(const double2* G, const int* col_src, int nq, const int* nbr,
+                        const int* nbond, const double* Jtab, const double* eps, const double* U,
+                        int Nr, int Nt, int Nc, int ncol, double dt, double* obs, cudaStream_t s);
+// [j][q*Nc+z'][z] -> user layout [q][j][z][z']
+void launch_export(const double2* G, int Nr, int Nc, int nq, double2* out, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+struct dyson_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int Lx = 0, Ly = 0, Nr = 0, Nb = 0, Nt = 0, Nm = 0, Nc = 0;
+  double dt = 0, beta = 0, curvature = 0, mu = 0;
+  std::vector<double> U, J;          // host copies of the drive tables
+
+  // device tables
+  double* dU = nullptr;              // [Nr][Nt]
+  double* dJ = nullptr;              // [Nb][Nt]
+  int* d_nbr = nullptr;              // [Nr][4] neighbour site or -1
+  int* d_nbond = nullptr;            // [Nr][4] bond index
+  double* d_eps = nullptr;           // [Nr]
+  double2* d_phase = nullptr;        // [Nr][2][Nc]
+  double2* d_lam = nullptr;          // [Nr][Nc][Nc]
+  double2* d_JW = nullptr;           // [Nb][Nc]
+  float* d_Jz = nullptr;             // [Nb][Nc]
+  float2* d_lam32 = nullptr;         // [Nr][Nc][Nc] (lazy)
+  float* d_lam_hi = nullptr;         // [Nr][2Nc][2Nc] (lazy)
+  float* d_lam_lo = nullptr;
+  double* d_obs = nullptr;           // [3][Nr][Nt]
+  bool sigma_built = false;
+
+  // work buffers, grown on demand
+  void* work = nullptr;
+  size_t work_bytes = 0;
+  int* d_col_src = nullptr;
+  int col_src_cap = 0;
+  unsigned long long* d_norm = nullptr;   // [2 * max block columns]
+  unsigned long long* h_norm = nullptr;   // pinned mirror
+  int norm_cap = 0;
+
+  bool lam32_built = false;
+  bool lam_split_built = false;
+  bool tc_enabled = true;            // 3xTF32 tcgen05 sweep allowed (DYSON_NO_TC=1 disables)
+  bool use_tc = false;               // chosen for the current solve
+  int max_refinements = 12;
+  int chunk_override = 0;
+
+  // optional per-launch event timing
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool profiling = false;
+  std::vector<Pending> pending;
+  double prof_ms[DYSON_KERNEL_KINDS] = {};
+  int64_t prof_launches[DYSON_KERNEL_KINDS] = {};
+
+  void* tc = nullptr;                // tensor-core module state (tensor maps, workspace)
+
+  std::string err;
+};
+
+int ctx_fail(dyson_ctx* c, int code, const std::string& msg);
+#define DY_CUDA(ctx, call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ctx_fail((ctx), e_ == cudaErrorMemoryAllocation ? DYSON_ERR_OOM : DYSON_ERR_CUDA, \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));              \
+  } while (0)

@@ -1,0 +1,12 @@
+// Tensor-core (tcgen05) sweep: interface used by the host driver.
+#pragma once
+#include "common.cuh"
+
+// true when the 3xTF32 tcgen05 sweep supports this contour length
+bool tc_supported(dyson_ctx* c, int Nc);
+// one sweep d_out = r + K d_in over the FP32 planar chunk state; writes c->d_norm[q]
+int tc_sweep(dyson_ctx* c, int nq, const float* r, const float* d_in, float* d_out);
+// DYSON_ERR_TIMEOUT if a bounded pipeline wait of an earlier sweep expired (clears the flag)
+int tc_check_error(dyson_ctx* c);
+// free tensor-core module state
+void tc_release(dyson_ctx* c);

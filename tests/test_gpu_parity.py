@@ -1,0 +1,181 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Floating-point tolerances:
+* FP64 path: 1e-12 relative (max-norm over the compared block, relative to its
+  max-norm) on problems whose series partial sums stay O(1);
+* mixed-precision path with FP64 residual refinement to tol: the same 1e-12
+  bound, since the refined result is fixed by the FP64 residual;
+* full-size sampled checks: 1e-6 relative on G and on densities, the bound for
+  reduced-precision paths.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import dyson, observables
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _solver(p):
+    from paper_1309_5994_gb300 import binding
+    s = binding.Solver(p, device=0)
+    s.build_sigma()
+    return s
+
+
+def _solve(torch, s, p, sources, prec, tol=1e-13, max_sweeps=400, allow=(0,)):
+    g = torch.empty((len(sources), p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda:0")
+    res = s.solve(sources, precision=prec, tol=tol, max_sweeps=max_sweeps, g_out=g, allow=allow)
+    return g.cpu().numpy(), res
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+SMALL = [
+    dict(L=3, Ly=2, Nt=7, Nm=5, trap_c=0.3, aU=0.1, aJ=0.2, omega=6.0),     # Nc = 19: ragged tiles
+    dict(L=2, Ly=2, Nt=3, Nm=1, beta=0.5),                                    # Nm = 1
+    dict(L=5, Ly=1, Nt=40, Nm=20, trap_c=0.1),                                # chain, Nc = 100 (2 tiles)
+    dict(L=1, Ly=1, Nt=10, Nm=6),                                             # one site: no bonds, G = Lambda
+]
+
+
+@pytest.mark.parametrize("kw", SMALL)
+def test_sigma_matches_oracle(torch_cuda, lib, kw):
+    p = wl.small(**kw)
+    S = dyson.setup(p)
+    s = _solver(p)
+    got = s.sigma()
+    assert _rel(got, S.Lam) < 1e-13
+
+
+def test_sigma_config1(torch_cuda, lib):
+    p = wl.config1()
+    S = dyson.setup(p)
+    s = _solver(p)
+    assert _rel(s.sigma(), S.Lam) < 1e-13
+
+
+@pytest.mark.parametrize("kw", SMALL)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_small_matches_dense(torch_cuda, lib, kw, prec):
+    p = wl.random_tables(wl.small(**kw), seed=7, rel=0.2)
+    S = dyson.setup(p)
+    sources = list(range(p.Nr)) + [0]        # every site, plus a repeat
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    s = _solver(p)
+    got, res = _solve(torch_cuda, s, p, sources, prec, tol=1e-13)
+    for q in range(len(sources)):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+    if p.Nr == 1:
+        assert np.array_equal(got[0][0], S.Lam[0]) or _rel(got[0][0], S.Lam[0]) < 1e-15
+
+
+TC_CASES = [
+    dict(L=2, Ly=2, Nt=24, Nm=16, trap_c=0.3, U0=20.0),                     # Nc = 64: one M tile per half
+    dict(L=3, Ly=2, Nt=40, Nm=48, trap_c=0.2, U0=16.0, aU=0.1, aJ=0.2, omega=20.0),   # Nc = 128
+    dict(L=1, Ly=3, Nt=72, Nm=48, trap_c=0.1, U0=20.0),                     # Nc = 192: 3 M tiles
+]
+
+
+@pytest.mark.parametrize("kw", TC_CASES)
+def test_tensor_core_path_matches_dense(torch_cuda, lib, kw):
+    """Contour lengths that are multiples of 64 run the 3xTF32 tcgen05 sweep."""
+    p = wl.random_tables(wl.small(**kw), seed=11, rel=0.2)
+    S = dyson.setup(p)
+    sources = list(range(p.Nr))
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    s = _solver(p)
+    s.profile(True)
+    got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
+    launches, _ = s.profile_query(2)
+    assert launches > 0                                     # the tensor-core kernel ran
+    for q in range(len(sources)):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config1_all_columns_and_observables(torch_cuda, lib, prec):
+    p = wl.config1()
+    S = dyson.setup(p)
+    sources = list(range(p.Nr))
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    s = _solver(p)
+    got, res = _solve(torch_cuda, s, p, sources, prec, tol=1e-13)
+    for q in range(p.Nr):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+    n, ekin, D = s.observables()
+    for i in range(p.Nr):
+        n_r, e_r, D_r = observables.observables_block_column(S, i, ref[:, :, i * p.Nc:(i + 1) * p.Nc])
+        assert np.abs(n[i] - n_r).max() < 1e-12
+        assert np.abs(ekin[i] - e_r).max() < 1e-12
+        assert np.isnan(D[i, 0]) and np.abs(D[i, 1:] - D_r[1:]).max() < 1e-10
+
+
+def test_unsolved_sites_report_nan(torch_cuda, lib):
+    p = wl.small(L=3, Nt=5, Nm=4)
+    s = _solver(p)
+    s.solve([4], precision=0)
+    n, _, _ = s.observables()
+    assert np.all(np.isfinite(n[4])) and np.all(np.isnan(np.delete(n, 4, axis=0)))
+
+
+def test_error_codes(torch_cuda, lib):
+    from paper_1309_5994_gb300 import binding
+    p = wl.small(L=3, Nt=5, Nm=4)
+    s = binding.Solver(p, device=0)
+    with pytest.raises(binding.DysonError) as e:
+        s.solve([0])
+    assert e.value.code == -7                               # solve before build_sigma
+    s.build_sigma()
+    with pytest.raises(binding.DysonError) as e:
+        s.solve([p.Nr])
+    assert e.value.code == -1                               # source out of range
+    r = s.solve([0], max_sweeps=1, allow=(-3,))
+    assert r.status == -3 and r.report["sweeps"] == 1       # not converged, results still written
+
+
+def test_slow_series_reports_not_converged(torch_cuda, lib):
+    """One imaginary point at beta = 1 puts the Matsubara block's spectral radius
+    at 0.997: the series needs thousands of sweeps and the solve says so."""
+    p = wl.small(L=2, Ly=2, Nt=3, Nm=1)
+    s = _solver(p)
+    for prec in (0, 1):
+        r = s.solve([0, 1], precision=prec, tol=1e-12, max_sweeps=50, allow=(-3,))
+        assert r.status == -3
+    n, _, _ = s.observables()
+    assert np.all(np.isfinite(n[:2]))
+
+
+def test_config2_sampled_columns_mixed(torch_cuda, lib):
+    """16x16 lattice, Nc = 256, the benchmark's launch shape: sampled vector
+    columns of two block columns against the oracle's complex128 series."""
+    p = wl.config2()
+    S = dyson.setup(p)
+    s = _solver(p)
+    sources = [0, 119]                                       # a corner and a near-centre site
+    got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-10, max_sweeps=300)
+    rng = np.random.default_rng(3)
+    cols = [(q, int(z)) for q in range(2) for z in rng.choice(p.Nc, 3, replace=False)]
+    B = dyson.rhs_vector_columns(S, [(sources[q], z) for q, z in cols])
+    ref, _, _ = dyson.neumann_solve(S, B, tol=1e-15, max_sweeps=400)
+    assert dyson.residual(S, B, ref) < 1e-11
+    for c, (q, z) in enumerate(cols):
+        assert _rel(got[q][:, :, z], ref[:, :, c]) < 1e-6
+    # densities of the source sites at all forward times
+    n, _, _ = s.observables()
+    i = sources[1]
+    Bn = dyson.rhs_vector_columns(S, [(i, k) for k in range(p.Nt)])
+    Gn, _, _ = dyson.neumann_solve(S, Bn, tol=1e-15, max_sweeps=400)
+    n_ref = np.array([np.real(-1j * Gn[i, k, k]) for k in range(p.Nt)])
+    assert np.abs(n[i] - n_ref).max() / np.abs(n_ref).max() < 1e-6
