@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark of the lattice Dyson solve on GB300.
+
+Workload: the 16x16 trapped lattice on the Nc = 256 contour (112 + 112 real-time
+points, dt = 0.05, 32 imaginary points, beta = 2, U = 20, J = 1, trap
+0.02 |r|^2, mu = 0): every block column G(:, s) solved to a relative FP64 Dyson
+residual <= tol with the mixed-precision path (3xTF32 tcgen05 series sweeps,
+FP64 residual refinement).  A step builds Lambda, solves one batch of
+`--batch` block columns (disjoint per rank and per step, cycling through the
+256 sources) and computes the observables of those sources; the metric is
+block columns per second over all ranks.
+
+Also measured: the same steps end to end through the C ABI from host buffers
+(e2e), the plain FP64 GPU series on two block columns (speed-up and the error
+of the mixed result against it), and the CPU oracle on a bounded sample
+(cpu_baseline).  `--impl reference` times the CPU oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "contour-GEMM TFLOP/s and G columns/s vs plain FP64 on one GB300 at rel err 1e-6"
+UNIT = "block columns/s"
+WORKLOAD = ("16x16 trapped lattice (256 sites, open boundaries), Nc=256 (112+112 real-time points dt=0.05, "
+            "32 imaginary), U=20, J=1, V=0.02|r|^2, mu=0, beta=2; all 256 block columns cycled in batches")
+# Measured peaks of this GPU (MEASURED_PEAKS.json, burst) and the recipe's nominal ratios
+NOMINAL_TF32_OVER_BF16 = 1.1 / 2.25
+NOMINAL_FP64_TFLOPS = 1.25          # 152 SMs x 4 FP64 flop/clk x 2.07 GHz (recipe's nominal FP64 rate)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--batch", type=int, default=16, help="block columns per step per GPU")
+    ap.add_argument("--tol", type=float, default=1e-10, help="relative FP64 Dyson residual")
+    ap.add_argument("--f64-columns", type=int, default=2, help="block columns timed on the plain FP64 path")
+    ap.add_argument("--cpu-columns", type=int, default=32, help="vector columns in the CPU oracle sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU legs (profiling runs)")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        self.index = ids[local_rank] if local_rank < len(ids) and ids[local_rank].strip().isdigit() else str(local_rank)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------
+def oracle_sample(p, site: int, zps, S=None):
+    """Time the CPU oracle's complex128 series on vector columns (site, z') of p."""
+    from oracle import dyson
+    if S is None:
+        S = dyson.setup(p)
+    B = dyson.rhs_vector_columns(S, [(site, int(z)) for z in zps])
+    t = time.perf_counter()
+    # 1e-12: the complex128 series' update settles near 1e-13 on this contour
+    G, sweeps, _ = dyson.neumann_solve(S, B, tol=1e-12, max_sweeps=400)
+    dt = time.perf_counter() - t
+    return dt, sweeps, S
+
+
+def blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(p, ncols: int):
+    import numpy as np
+    zps = np.linspace(0, p.Nc - 1, ncols).astype(int)
+    dt, sweeps, _ = oracle_sample(p, 119, zps)
+    per_block = dt * p.Nc / ncols
+    return {"value": 1.0 / per_block, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+            "sample": (f"{ncols} of the 256 vector columns of block column 119, complex128 series to 1e-12 "
+                       f"({sweeps} sweeps, {dt:.2f} s), scaled linearly to one block column")}
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import workloads as wl
+    from oracle import dyson
+    p = wl.config2()
+    S = dyson.setup(p)
+    ncols = 16
+    times = []
+    for step in range(args.warmup + args.steps):
+        site = (step * 37) % p.Nr
+        zps = np.linspace(step % 16, p.Nc - 1, ncols).astype(int)
+        dt, _, _ = oracle_sample(p, site, zps, S)
+        if step >= args.warmup:
+            times.append(dt * p.Nc / ncols)      # seconds per block column
+    per_block = sum(times) / len(times)
+    value = 1.0 / per_block
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_block * 1e3 * ncols / p.Nc,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": f"{ncols} vector columns of one block column"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                             "sample": f"{ncols} vector columns per step, complex128 series, scaled to block columns"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gb300(args, rank, world, local):
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_1309_5994_gb300 import binding, dist
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = wl.config2()
+    stream = torch.cuda.Stream(device=dev)
+    solver = binding.Solver(p, device=local, stream=stream)
+    PREC = binding.PREC_TF32X3_F64REF
+
+    def step(k, s=solver):
+        src = dist.step_sources(p.Nr, args.batch, rank, world, k)
+        s.build_sigma()
+        return s.solve(src, precision=PREC, tol=args.tol, max_sweeps=400)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    dist.barrier(local)
+
+    # ---- timed region: device events on the library stream ----
+    solver.profile(True)
+    launches0 = solver.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    ev0.record(stream)
+    reports = []
+    for k in range(args.steps):
+        reports.append(step(args.warmup + k).report)
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    dist.barrier(local)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    gpu_launches = solver.launch_count() - launches0
+    kstats = {binding.KERNEL_NAMES[kk]: solver.profile_query(kk) for kk in range(4)}
+    solver.profile(False)
+    max_ms = dist.max_over_ranks(elapsed_ms, device=dev)
+
+    cols_total = world * args.steps * args.batch
+    value = cols_total / (max_ms * 1e-3)
+    flops = sum(r["gemm_flops"] for r in reports)
+    tflops_local = flops / (elapsed_ms * 1e-3) / 1e12
+    sweeps = [r["sweeps"] for r in reports]
+    refinements = [r["refinements"] for r in reports]
+    residual = max(r["residual"] for r in reports)
+
+    # ---- roofline of the kernel with the largest device time ----
+    peaks, peak_src = load_peaks()
+    Nc, Nr = p.Nc, p.Nr
+    alg_flops_per_launch = 8.0 * Nc ** 3 * Nr * args.batch
+    dom_name, (dom_n, dom_ms) = max(kstats.items(), key=lambda kv: kv[1][1])
+    achieved = alg_flops_per_launch / (dom_ms / dom_n * 1e-3) / 1e12 if dom_n else 0.0
+    if dom_name == "residual_f64" or dom_name == "sweep_f64":
+        roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 rate from SM count x FP64 flop/clk x max clock (no measured FP64 peak)"}
+    else:
+        peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None,
+                "peak_source": f"{peak_src} bf16 burst x nominal tf32/bf16 ratio; achieved counts algorithmic "
+                               f"complex-GEMM flops (8 Nc^3 per site and block column), the 3xTF32 split executes 3x"}
+    roof["kernel"] = dom_name
+    kernels = {nm: {"launches": n, "avg_ms": (ms / n if n else None), "total_ms": ms,
+                    "share": ms / max(sum(v[1] for v in kstats.values()), 1e-9)}
+               for nm, (n, ms) in kstats.items() if n}
+
+    extras = {}
+    if not args.no_extras:
+        # ---- e2e through the C ABI from host buffers: init (tables H2D), build, solve, observables D2H ----
+        h2d = p.U.nbytes + p.J.nbytes + 4 * args.batch
+        d2h = 3 * p.Nr * p.Nt * 8
+        torch.cuda.synchronize(dev)
+        dist.barrier(local)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            s2 = binding.Solver(p, device=local, stream=stream)
+            s2.build_sigma()
+            s2.solve(dist.step_sources(p.Nr, args.batch, rank, world, k), precision=PREC, tol=args.tol,
+                     max_sweeps=400)
+            s2.observables()
+            s2.close()
+        torch.cuda.synchronize(dev)
+        e2e_s = dist.max_over_ranks(time.perf_counter() - t0, device=dev)
+        extras["e2e"] = {"value": cols_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                         "d2h_bytes_per_step": d2h}
+        if rank == 0:
+            # ---- plain FP64 GPU series on a few block columns, and the mixed result's error ----
+            nf = args.f64_columns
+            srcs = list(range(nf))
+            g64 = torch.empty((nf, Nr, Nc, Nc), dtype=torch.complex128, device=dev)
+            gmx = torch.empty_like(g64)
+            solver.build_sigma()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            # the FP64 series update bottoms out near 1e-13 on this contour (rounding of
+            # partial sums that peak ~200x above the result), so 1e-12 is its reachable target
+            r64 = solver.solve(srcs, precision=binding.PREC_F64, tol=1e-12, max_sweeps=400, g_out=g64,
+                               allow=(0, -3))
+            torch.cuda.synchronize(dev)
+            t64 = time.perf_counter() - t0
+            n64, _, _ = solver.observables()
+            rmx = solver.solve(srcs, precision=PREC, tol=args.tol, max_sweeps=400, g_out=gmx)
+            nmx, _, _ = solver.observables()
+            den = torch.abs(g64).max().item()
+            gerr = torch.abs(gmx - g64).max().item() / den
+            gii = torch.stack([g64[q, s] for q, s in enumerate(srcs)])
+            gii_m = torch.stack([gmx[q, s] for q, s in enumerate(srcs)])
+            gii_err = (torch.abs(gii_m - gii).max() / torch.abs(gii).max()).item()
+            nerr = float(np.abs(nmx[srcs] - n64[srcs]).max() / np.abs(n64[srcs]).max())
+            f64_rate = nf / t64
+            extras["plain_f64"] = {"value": f64_rate, "unit": UNIT, "block_columns": nf,
+                                   "sweeps": r64.report["sweeps"], "status": r64.status,
+                                   "final_update": r64.report["update"],
+                                   "tflops": r64.report["gemm_flops"] / t64 / 1e12}
+            extras["speedup_vs_plain_f64"] = (value / world) / f64_rate
+            extras["rel_err_vs_plain_f64"] = {"G": gerr, "G_ii": gii_err, "density": nerr}
+            del g64, gmx
+            if world == 1:
+                extras["cpu_baseline"] = cpu_baseline(p, args.cpu_columns)
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "block_columns_per_step_per_gpu": args.batch,
+                       "precision": "3xTF32 tcgen05 series sweeps + FP64 Dyson residual refinement",
+                       "tol_rel_residual": args.tol, "lattice": [p.Lx, p.Ly], "Nc": Nc,
+                       "l2": f"inputs larger than L2: {48 * Nr * Nc * Nc * args.batch / 1e9:.1f} GB of state per step",
+                       "parallelism": f"block columns sharded over {world} GPU(s), no data-path collective"},
+            "contour_gemm_tflops": tflops_local * world,
+            "vector_columns_per_s": value * Nc,
+            "sweeps_per_step": sweeps, "refinements_per_step": refinements, "max_rel_residual": residual,
+            "roofline": roof, "kernels": kernels, "clocks": clk, "gpu_launches": gpu_launches}
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    from paper_1309_5994_gb300 import dist
+    rank, world, local = dist.env_ranks()
+    if args.impl == "reference":
+        run_reference(args, rank, world)      # rank 0 only; other ranks exit without work
+        return
+    dist.init("nccl")
+    run_gb300(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -95,6 +95,7 @@ typedef struct {
   double gemm_flops;            /* algorithmic contour-GEMM flops: 8 Nc^3 per site,
                                    block column and sweep, over every sweep performed      */
   double seconds;               /* wall time of the call                                   */
+  int64_t kernel_launches;      /* CUDA kernels this call launched                         */
 } dyson_report;
 
 /* Create a context on `device`, ordering work on `cuda_stream` (a cudaStream_t,
@@ -158,6 +159,9 @@ int dyson_profile(dyson_ctx* ctx, int enable);
 /* Launch count and summed device time (ms) of one DYSON_KERNEL_* kind since
  * the last dyson_profile call. */
 int dyson_profile_query(dyson_ctx* ctx, int kind, int64_t* launches, double* total_ms);
+
+/* CUDA kernels launched by this context since dyson_init (-1 for NULL). */
+int64_t dyson_launch_count(const dyson_ctx* ctx);
 
 /* Cap the number of block columns solved together (0 = size from free memory). */
 int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);

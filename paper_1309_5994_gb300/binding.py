@@ -43,7 +43,7 @@ class Drive(C.Structure):
 class Report(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("refinements", C.c_int32), ("chunks", C.c_int32),
                 ("status", C.c_int32), ("update", C.c_double), ("residual", C.c_double),
-                ("gemm_flops", C.c_double), ("seconds", C.c_double)]
+                ("gemm_flops", C.c_double), ("seconds", C.c_double), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -51,7 +51,7 @@ class Report(C.Structure):
 
 EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_columns",
            "dyson_observables", "dyson_profile", "dyson_profile_query", "dyson_set_chunk",
-           "dyson_destroy", "dyson_last_error", "dyson_version"]
+           "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version"]
 
 
 def load(path: str = _LIB_PATH):
@@ -73,6 +73,8 @@ def load(path: str = _LIB_PATH):
     lib.dyson_profile.argtypes = [P, C.c_int]
     lib.dyson_profile_query.argtypes = [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     lib.dyson_set_chunk.argtypes = [P, C.c_int32]
+    lib.dyson_launch_count.argtypes = [P]
+    lib.dyson_launch_count.restype = C.c_int64
     lib.dyson_destroy.argtypes = [P]
     lib.dyson_destroy.restype = None
     lib.dyson_last_error.argtypes = [P]
@@ -161,6 +163,9 @@ class Solver:
     def observables_device(self, n, ekin, docc):
         self._check(self.lib.dyson_observables(self.h, C.c_void_p(n.data_ptr()), C.c_void_p(ekin.data_ptr()),
                                                C.c_void_p(docc.data_ptr()), 1))
+
+    def launch_count(self) -> int:
+        return int(self.lib.dyson_launch_count(self.h))
 
     def set_chunk(self, cols: int):
         self._check(self.lib.dyson_set_chunk(self.h, cols))

@@ -136,6 +136,7 @@ int solve_f64(dyson_ctx* c, int nq, double tol, int max_sweeps, double2** result
   DY_CUDA(c, cudaMemsetAsync(Ga, 0, n_el * sizeof(double2), c->stream));
   DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, 2 * (size_t)nq * sizeof(unsigned long long), c->stream));
   launch_init_rhs(c->d_lam, c->d_col_src, c->Nr, c->Nc, (int)ncol, Ga, c->d_norm + nq, c->stream);
+  c->launches += 1;
   int rc = read_norms(c, nq, true);
   if (rc) return rc;
   std::vector<double> scale(nq);
@@ -147,6 +148,7 @@ int solve_f64(dyson_ctx* c, int nq, double tol, int max_sweeps, double2** result
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F64);
       launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, Ga, Gb, nullptr, c->d_col_src, c->Nr, c->Nc,
                        (int)ncol, 0, c->d_norm, c->stream);
+      c->launches += 1;
     }
     DY_CUDA(c, cudaGetLastError());
     if ((rc = read_norms(c, nq, false))) return rc;
@@ -184,6 +186,7 @@ int inner_solve(dyson_ctx* c, int nq, int precision, float* r32, float* da, floa
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
       launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, (int)ncol,
                             c->d_norm, c->stream);
+      c->launches += 1;
     }
     DY_CUDA(c, cudaGetLastError());
     if ((rc = read_norms(c, nq, false))) return rc;
@@ -226,6 +229,7 @@ int solve_mixed(dyson_ctx* c, int nq, int precision, double tol, int max_sweeps,
   DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, 2 * (size_t)nq * sizeof(unsigned long long), c->stream));
   launch_init_rhs(c->d_lam, c->d_col_src, c->Nr, c->Nc, (int)ncol, G, c->d_norm + nq, c->stream);
   launch_to_planar32(G, r32, n_el, c->Nc, c->stream);
+  c->launches += 2;
   DY_CUDA(c, cudaMemsetAsync(G, 0, n_el * sizeof(double2), c->stream));
   if ((rc = read_norms(c, nq, true))) return rc;
   std::vector<double> scale(nq), rref(nq);
@@ -235,11 +239,13 @@ int solve_mixed(dyson_ctx* c, int nq, int precision, double tol, int max_sweeps,
     float* d = nullptr;
     if ((rc = inner_solve(c, nq, precision, r32, da, db, max_sweeps, rref, &d, rep))) return rc;
     launch_accumulate(G, d, c->Nr, c->Nc, (int)ncol, c->stream);
+    c->launches += 1;
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)nq * sizeof(unsigned long long), c->stream));
     {
       KernelTimer t(c, DYSON_KERNEL_RESIDUAL_F64);
       launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, G, nullptr, r32, c->d_col_src, c->Nr, c->Nc,
                        (int)ncol, 1, c->d_norm, c->stream);
+      c->launches += 1;
     }
     DY_CUDA(c, cudaGetLastError());
     if ((rc = read_norms(c, nq, false))) return rc;
@@ -365,6 +371,7 @@ int dyson_build_sigma(dyson_ctx* c) {
   launch_build_sigma(c->dU, c->Lx, c->Ly, c->Nt, c->Nm, c->dt, c->beta, c->curvature, c->mu, c->d_eps,
                      c->d_phase, c->d_lam, c->stream);
   launch_hopping_tables(c->dJ, c->Nb, c->Nt, c->Nm, c->dt, c->beta, c->d_JW, c->d_Jz, c->stream);
+  c->launches += c->Nb > 0 ? 3 : 2;
   DY_CUDA(c, cudaGetLastError());
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
   c->sigma_built = true;
@@ -388,8 +395,10 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
   dyson_report rep;
   std::memset(&rep, 0, sizeof rep);
   auto t0 = std::chrono::steady_clock::now();
+  const int64_t launches0 = c->launches;
   auto finish = [&](int code) {
     rep.status = code;
+    rep.kernel_launches = c->launches - launches0;
     rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (rep_out) *rep_out = rep;
     return code;
@@ -407,6 +416,7 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
     if (!c->lam32_built && (!c->tc_enabled || !tc_supported(c, c->Nc))) {
       if (!c->d_lam32) DY_CUDA(c, dalloc(&c->d_lam32, (size_t)c->Nr * c->Nc * c->Nc));
       launch_lam_c64(c->d_lam, c->Nr, c->Nt, c->Nm, c->dt, c->beta, c->d_lam32, c->stream);
+      c->launches += 1;
       c->lam32_built = true;
     }
     if (c->tc_enabled && tc_supported(c, c->Nc) && !c->lam_split_built) {
@@ -414,6 +424,7 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
       if (!c->d_lam_hi) DY_CUDA(c, dalloc(&c->d_lam_hi, n));
       if (!c->d_lam_lo) DY_CUDA(c, dalloc(&c->d_lam_lo, n));
       launch_lam_emb_split(c->d_lam, c->Nr, c->Nt, c->Nm, c->dt, c->beta, c->d_lam_hi, c->d_lam_lo, c->stream);
+      c->launches += 1;
       c->lam_split_built = true;
     }
     c->use_tc = c->tc_enabled && tc_supported(c, c->Nc);
@@ -448,7 +459,11 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
     rep.chunks += 1;
     launch_observables(G, c->d_col_src, nq, c->d_nbr, c->d_nbond, c->dJ, c->d_eps, c->dU, c->Nr, c->Nt, c->Nc,
                        (int)ncol, c->dt, c->d_obs, c->stream);
-    if (g_out) launch_export(G, c->Nr, c->Nc, nq, (double2*)g_out + (size_t)start * c->Nr * c->Nc * c->Nc, c->stream);
+    c->launches += 1;
+    if (g_out) {
+      launch_export(G, c->Nr, c->Nc, nq, (double2*)g_out + (size_t)start * c->Nr * c->Nc * c->Nc, c->stream);
+      c->launches += 1;
+    }
     DY_CUDA(c, cudaGetLastError());
   }
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -489,6 +504,8 @@ int dyson_profile_query(dyson_ctx* c, int kind, int64_t* launches, double* total
   if (total_ms) *total_ms = c->prof_ms[kind];
   return DYSON_OK;
 }
+
+int64_t dyson_launch_count(const dyson_ctx* c) { return c ? c->launches : -1; }
 
 int dyson_set_chunk(dyson_ctx* c, int32_t block_columns) {
   if (!c || block_columns < 0) return fail_noctx(DYSON_ERR_INVALID_ARG, "bad chunk size");

@@ -108,6 +108,7 @@ struct dyson_ctx {
   bool use_tc = false;               // chosen for the current solve
   int max_refinements = 12;
   int chunk_override = 0;
+  int64_t launches = 0;              // kernels launched by this context since dyson_init
 
   // optional per-launch event timing
   struct Pending {

@@ -77,8 +77,8 @@ def test_solve_small_matches_dense(torch_cuda, lib, kw, prec):
     got, res = _solve(torch_cuda, s, p, sources, prec, tol=1e-13)
     for q in range(len(sources)):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
-    if p.Nr == 1:
-        assert np.array_equal(got[0][0], S.Lam[0]) or _rel(got[0][0], S.Lam[0]) < 1e-15
+    if p.Nr == 1:                            # no bonds: G = Lambda, up to the Lambda build's rounding
+        assert _rel(got[0][0], S.Lam[0]) < 1e-13
 
 
 TC_CASES = [
