@@ -166,6 +166,45 @@ int64_t dyson_launch_count(const dyson_ctx* ctx);
 /* Cap the number of block columns solved together (0 = size from free memory). */
 int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free solve of one block column.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * while they run (a device heap owned and pre-reserved by another framework's
+ * pool, latency-bound loops where cudaMalloc's implicit synchronisation is not
+ * acceptable, tools that may not change a library's memory footprint).
+ *
+ * It runs the same FP64 series as dyson_solve_columns(precision = F64) for one
+ * source site, but its only scratch memory (one block-column state and two
+ * norm words) is a file-scope device array of DYSON_NOALLOC_MAX_STATE_BYTES +
+ * 256 bytes that every GPU loading the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *   lambda  device, [Nr][Nc][Nc] complex128 Lambda (e.g. from dyson_copy_sigma
+ *           with on_device = 1);
+ *   J       device, [Nb][Nt] hopping table (bond order as above; may be NULL
+ *           when Nr = 1);
+ *   g_out   device, [Nr][Nc][Nc] complex128, receives G_js(z, z') at [j][z][z'];
+ *   sweeps_out  host, optional: sweeps performed;
+ *   work is ordered on cuda_stream (NULL: legacy default stream) of the
+ *   current device, and the call returns after it has completed.
+ * Sizes with Nr*Nc*Nc*16 > DYSON_NOALLOC_MAX_STATE_BYTES are rejected with
+ * INVALID_ARG (see dyson_noalloc_last_error).  Returns OK, NOT_CONVERGED
+ * (g_out holds the last iterate), DIVERGED, INVALID_ARG or CUDA.
+ *
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.  All calls share the one array and it keeps the
+ * previous call's contents (the call clears what must start at zero): calls
+ * that overlap on the GPU, from several threads or streams, race on it. */
+#define DYSON_NOALLOC_MAX_STATE_BYTES (16u << 20)
+
+int dyson_solve_block_column_noalloc(const double* lambda, const double* J, int32_t Lx, int32_t Ly, int32_t Nt,
+                                     int32_t Nm, double dt, double beta, int32_t source, double tol,
+                                     int32_t max_sweeps, double* g_out, int32_t* sweeps_out, void* cuda_stream);
+
+/* Message of the last failing dyson_solve_block_column_noalloc call on this thread. */
+const char* dyson_noalloc_last_error(void);
+
 /* Library version string. */
 const char* dyson_version(void);
 

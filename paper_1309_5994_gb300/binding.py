@@ -51,7 +51,8 @@ class Report(C.Structure):
 
 EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_columns",
            "dyson_observables", "dyson_profile", "dyson_profile_query", "dyson_set_chunk",
-           "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version"]
+           "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
+           "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error"]
 
 
 def load(path: str = _LIB_PATH):
@@ -75,6 +76,10 @@ def load(path: str = _LIB_PATH):
     lib.dyson_set_chunk.argtypes = [P, C.c_int32]
     lib.dyson_launch_count.argtypes = [P]
     lib.dyson_launch_count.restype = C.c_int64
+    lib.dyson_solve_block_column_noalloc.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                                     C.c_double, C.c_int32, C.c_double, C.c_int32, P,
+                                                     C.POINTER(C.c_int32), P]
+    lib.dyson_noalloc_last_error.restype = C.c_char_p
     lib.dyson_destroy.argtypes = [P]
     lib.dyson_destroy.restype = None
     lib.dyson_last_error.argtypes = [P]
