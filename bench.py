@@ -219,7 +219,7 @@ def run_gb300(args, rank, world, local):
     dist.barrier(local)
     elapsed_ms = ev0.elapsed_time(ev1)
     gpu_launches = solver.launch_count() - launches0
-    kstats = {binding.KERNEL_NAMES[kk]: solver.profile_query(kk) for kk in range(4)}
+    kstats = {name: solver.profile_query(kk) for kk, name in binding.KERNEL_NAMES.items()}
     solver.profile(False)
     max_ms = dist.max_over_ranks(elapsed_ms, device=dev)
 
@@ -241,10 +241,16 @@ def run_gb300(args, rank, world, local):
         roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
                 "peak_source": "nominal FP64 rate from SM count x FP64 flop/clk x max clock (no measured FP64 peak)"}
+    elif dom_name == "residual_split_bf16":
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "executed_tflops": 28 * achieved,
+                "peak_source": f"{peak_src} bf16 burst; achieved counts algorithmic complex-GEMM flops "
+                               f"(8 Nc^3 per site and block column), the 7-slice split executes 28 BF16 products"}
     else:
         peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": None, "executed_tflops": 3 * achieved,
                 "peak_source": f"{peak_src} bf16 burst x nominal tf32/bf16 ratio; achieved counts algorithmic "
                                f"complex-GEMM flops (8 Nc^3 per site and block column), the 3xTF32 split executes 3x"}
     roof["kernel"] = dom_name

@@ -149,7 +149,8 @@ enum {
   DYSON_KERNEL_SWEEP_F32 = 1,     /* FP32 CUDA-core sweep                                    */
   DYSON_KERNEL_SWEEP_TC = 2,      /* 3xTF32 tcgen05 sweep (gather + split + GEMM)            */
   DYSON_KERNEL_RESIDUAL_F64 = 3,  /* FP64 Dyson residual r = Lambda delta + K G - G          */
-  DYSON_KERNEL_KINDS = 4
+  DYSON_KERNEL_RESIDUAL_SPLIT = 4,/* the same residual from BF16 slice products on tcgen05   */
+  DYSON_KERNEL_KINDS = 5
 };
 
 /* Enable (1) or disable (0) event timing of every sweep/residual launch on the

@@ -20,8 +20,9 @@ ERR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_CONVERGED", -4: "DI
              -6: "CUDA", -7: "STATE"}
 PREC_F64 = 0
 PREC_TF32X3_F64REF = 1
-KERNEL_SWEEP_F64, KERNEL_SWEEP_F32, KERNEL_SWEEP_TC, KERNEL_RESIDUAL_F64 = 0, 1, 2, 3
-KERNEL_NAMES = {0: "sweep_f64", 1: "sweep_f32_simt", 2: "sweep_tc_3xtf32", 3: "residual_f64"}
+KERNEL_SWEEP_F64, KERNEL_SWEEP_F32, KERNEL_SWEEP_TC, KERNEL_RESIDUAL_F64, KERNEL_RESIDUAL_SPLIT = 0, 1, 2, 3, 4
+KERNEL_NAMES = {0: "sweep_f64", 1: "sweep_f32_simt", 2: "sweep_tc_3xtf32", 3: "residual_f64",
+                4: "residual_split_bf16"}
 
 
 class Lattice(C.Structure):

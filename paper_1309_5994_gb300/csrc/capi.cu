@@ -7,6 +7,7 @@
 #include <limits>
 
 #include "common.cuh"
+#include "oz.cuh"
 #include "tc.cuh"
 
 namespace {
@@ -241,7 +242,10 @@ int solve_mixed(dyson_ctx* c, int nq, int precision, double tol, int max_sweeps,
     launch_accumulate(G, d, c->Nr, c->Nc, (int)ncol, c->stream);
     c->launches += 1;
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)nq * sizeof(unsigned long long), c->stream));
-    {
+    if (c->use_oz) {
+      KernelTimer t(c, DYSON_KERNEL_RESIDUAL_SPLIT);
+      if ((rc = oz_residual(c, nq, G, r32))) return rc;
+    } else {
       KernelTimer t(c, DYSON_KERNEL_RESIDUAL_F64);
       launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, G, nullptr, r32, c->d_col_src, c->Nr, c->Nc,
                        (int)ncol, 1, c->d_norm, c->stream);
@@ -249,6 +253,7 @@ int solve_mixed(dyson_ctx* c, int nq, int precision, double tol, int max_sweeps,
     }
     DY_CUDA(c, cudaGetLastError());
     if ((rc = read_norms(c, nq, false))) return rc;
+    if (c->use_oz && (rc = oz_check_error(c))) return rc;
     rep->refinements += 1;
     rep->gemm_flops += 8.0 * c->Nc * (double)c->Nc * c->Nc * c->Nr * nq;
     double res = rel_max(c->h_norm, scale.data(), nq);
@@ -326,6 +331,7 @@ int dyson_init(dyson_ctx** out, const dyson_lattice* L, const dyson_contour* C, 
     }
   if (const char* e = std::getenv("DYSON_MAX_REFINEMENTS")) c->max_refinements = std::max(1, atoi(e));
   if (const char* e = std::getenv("DYSON_NO_TC")) c->tc_enabled = !(e[0] == '1');
+  if (const char* e = std::getenv("DYSON_NO_OZ")) c->oz_enabled = !(e[0] == '1');
 
   // neighbour slots (+x, -x, +y, -y) with their bond indices
   std::vector<int> nbr((size_t)c->Nr * 4, -1), nbond((size_t)c->Nr * 4, -1);
@@ -376,6 +382,7 @@ int dyson_build_sigma(dyson_ctx* c) {
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
   c->sigma_built = true;
   c->lam32_built = c->lam_split_built = false;
+  oz_invalidate(c);
   return DYSON_OK;
 }
 
@@ -433,7 +440,10 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
   // chunk size from free device memory (bytes per block column of work state)
   // F64: two complex128 states; mixed: complex128 G + three FP32 states (+ the
   // FP32 gather buffer of the tensor-core sweep)
-  const double per_el = precision == DYSON_PREC_F64 ? 32.0 : (c->use_tc ? 48.0 : 40.0);
+  c->use_oz = precision != DYSON_PREC_F64 && c->use_tc && c->oz_enabled && oz_supported(c);
+  const double per_el = precision == DYSON_PREC_F64
+                            ? 32.0
+                            : (c->use_tc ? 48.0 : 40.0) + (c->use_oz ? (double)oz_bytes_per_element() : 0.0);
   const double col_bytes = per_el * c->Nr * (double)c->Nc * c->Nc;
   size_t free_b = 0, total_b = 0;
   DY_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
@@ -519,6 +529,7 @@ void dyson_destroy(dyson_ctx* c) {
   cudaStreamSynchronize(c->stream);
   flush_timers(c);
   tc_release(c);
+  oz_release(c);
   void* ptrs[] = {c->dU, c->dJ, c->d_nbr, c->d_nbond, c->d_eps, c->d_phase, c->d_lam, c->d_JW, c->d_Jz,
                   c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_col_src, c->d_norm};
   for (void* p : ptrs)

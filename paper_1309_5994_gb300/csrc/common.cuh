@@ -121,6 +121,9 @@ struct dyson_ctx {
   int64_t prof_launches[DYSON_KERNEL_KINDS] = {};
 
   void* tc = nullptr;                // tensor-core module state (tensor maps, workspace)
+  void* oz = nullptr;                // split-product residual state (slices, scales, maps)
+  bool oz_enabled = true;            // DYSON_NO_OZ=1 keeps the FP64 CUDA-core residual
+  bool use_oz = false;               // chosen for the current solve
 
   std::string err;
 };

@@ -1,0 +1,472 @@
+// FP64-accurate Dyson residual on the BF16 tensor cores:
+//     r = B + (Lambda W) X - G,   X_i(n, k) = sum_{j in NN(i)} J_ij(k) G_j(n, k),
+// the residual of the series of App. C that refines the FP32 sweeps.
+//
+// The real GEMM A X (A = [[Re,-Im],[Im,Re]] of Lambda W, per site 2Nc x 2Nc) is
+// evaluated exactly enough in FP32 tensor-core arithmetic by splitting both
+// operands into integer slices (the Ozaki scheme): every row of A and every
+// column of X is scaled by a power of two into [-1, 1] and cut into S = 7 slices
+// of 7 bits, v = sum_s q_s 2^{-7 s} with integers |q_s| <= 128.  A slice product
+// sum_k A_s X_t is then an integer multiple of 2^{-7(s+t)} below 2^24 in
+// magnitude for every diagonal s + t <= 5 when K = 2Nc <= 512, so BF16 inputs
+// with FP32 accumulation are exact there.
+// The 28 products with s + t <= 8 (truncation ~2^-50 of |A||X|) accumulate per
+// diagonal in five TMEM accumulators, {2}, {3}, {4}, {5} exact and {6, 7, 8}
+// rounded at 2^-24 of its own size (about 2^-48 of the result).  The epilogue
+// adds them in FP64, rescales, and forms r = B + A X - G in FP64.
+//
+// Kernels: k_oz_aprep (once per Lambda), k_oz_xprep (gather + scale + slice of X
+// per residual), k_oz_gemm (TMA + tcgen05.mma kind::f16 + FP64 epilogue).
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "oz.cuh"
+#include "ptx.cuh"
+
+namespace {
+
+constexpr int S = 7;
+constexpr int BM = 128, BN = 96, BK = 32;                 // BK bf16 = 64-byte rows (64-byte swizzle)
+constexpr int A_TILE = BM * BK * 2;                       // 8 KB per A slice tile
+constexpr int X_TILE = BN * BK * 2;                       // 6 KB per X slice tile
+constexpr int STAGE_BYTES = S * (A_TILE + X_TILE);        // S A slices + S X slices (98 KB)
+constexpr int STAGES = 2;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int THREADS = 256;
+constexpr int NACC = 5;                                    // diagonals {2}, {3}, {4}, {5}, {6, 7, 8}
+constexpr uint32_t TMEM_COLS = 512;                        // 5 accumulators x 96 columns
+constexpr int NPROD = S * (S + 1) / 2;                     // products with s + t <= S + 1
+// kind::f16, D = F32, A = B = BF16, K-major, M = 128, N = 96
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct OzState {
+  CUtensorMap amap, xmap;
+  __nv_bfloat16* aslices = nullptr;   // [S][Nr][2Nc][2Nc]
+  double* sigma = nullptr;            // [Nr][2Nc] row scales of A
+  size_t a_bytes = 0;
+  bool a_ready = false;
+  __nv_bfloat16* xslices = nullptr;   // [S][Nr][ncol][2Nc]
+  double* tau = nullptr;              // [Nr][ncol] column scales of X
+  size_t x_bytes = 0, tau_bytes = 0;
+  const void* xmap_ptr = nullptr;
+  int xmap_ncol = -1;
+  int* d_err = nullptr;
+  bool smem_set = false;
+};
+
+__device__ __forceinline__ int time_of(int z, int Nt) { return z < Nt ? z : (z < 2 * Nt ? 2 * Nt - 1 - z : 0); }
+__device__ __forceinline__ double2 weight_of(int z, int Nt, int Nm, double dt, double beta) {
+  return z < Nt ? make_double2(dt, 0.0) : (z < 2 * Nt ? make_double2(-dt, 0.0) : make_double2(0.0, -beta / Nm));
+}
+
+// power of two >= max |v| (1 for an all-zero vector)
+__device__ __forceinline__ double pow2_scale(double mx) {
+  if (!(mx > 0.0)) return 1.0;
+  int e;
+  frexp(mx, &e);           // mx = f 2^e, f in [0.5, 1)
+  return ldexp(1.0, e);
+}
+
+constexpr int FIX = 7 * S;                                 // fixed-point bits of a scaled value
+
+// Write the S slices of x / sc (|x| <= sc, sc a power of two).  The value is
+// rounded once to the fixed-point integer V = rint(x 2^FIX / sc) (|V| <= 2^FIX),
+// then cut into signed 7-bit digits with integer shifts: slice s holds
+// q_s 2^{-7 s}, q_s = round(V_rem / 2^{7 (S - s)}), |q_1| <= 128, |q_s| <= 64.
+// Only one FP64 multiply and one conversion per value: FP64 is scarce here.
+__device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_bfloat16* dst, size_t slice_stride) {
+  long long V = __double2ll_rn(x * fix_over_sc);
+#pragma unroll
+  for (int s = 1; s <= S; ++s) {
+    const int sh = 7 * (S - s);
+    const long long q = sh ? ((V + (1LL << (sh - 1))) >> sh) : V;
+    V -= q << sh;
+    const float part = __int2float_rn((int)q) * __int_as_float((127 - 7 * s) << 23);   // q * 2^{-7 s}, exact
+    dst[(size_t)(s - 1) * slice_stride] = __float2bfloat16_rn(part);
+  }
+}
+
+// rint(f * 2^FIX) for an FP32 accumulator value, by integer arithmetic on its bits
+__device__ __forceinline__ long long f32_to_fixed(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const int e = (int)((b >> 23) & 0xFF);
+  if (e == 0) return 0;                                    // zero (denormals are far below 2^-FIX)
+  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = e - 150 + FIX;                            // f 2^FIX = m 2^sh
+  long long v;
+  if (sh >= 0) v = m << sh;                                // exact: |f| < 2^10 keeps this below 2^63
+  else if (sh > -40) v = (m + (1LL << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return (b >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ double emb_value(const double2* lrow, int k, int part, int Nc, int Nt, int Nm, double dt,
+                                            double beta) {
+  int kb = k < Nc ? k : k - Nc, kpart = k < Nc ? 0 : 1;
+  double2 v = cmul(lrow[kb], weight_of(kb, Nt, Nm, dt, beta));
+  return part == kpart ? v.x : (part == 0 ? -v.y : v.y);
+}
+
+// one warp per row (site i, row m) of the embedding of Lambda W
+__global__ void k_oz_aprep(const double2* __restrict__ lam, int Nr, int Nt, int Nm, double dt, double beta,
+                           __nv_bfloat16* __restrict__ as, double* __restrict__ sigma) {
+  const int Nc = 2 * Nt + Nm, N2 = 2 * Nc;
+  const size_t row = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= (size_t)Nr * N2) return;
+  const int i = (int)(row / N2), m = (int)(row % N2);
+  const int z = m % Nc, part = m / Nc;
+  const double2* lrow = lam + ((size_t)i * Nc + z) * Nc;
+  double mx = 0.0;
+  for (int k = lane; k < N2; k += 32) mx = fmax(mx, fabs(emb_value(lrow, k, part, Nc, Nt, Nm, dt, beta)));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const double sc = pow2_scale(mx);
+  if (lane == 0) sigma[row] = sc;
+  const double fix_over_sc = ldexp(1.0, FIX) / sc;
+  const size_t stride = (size_t)Nr * N2 * N2;
+  for (int k = lane; k < N2; k += 32)
+    write_slices(emb_value(lrow, k, part, Nc, Nt, Nm, dt, beta), fix_over_sc, as + row * N2 + k, stride);
+}
+
+// one warp per (site i, vector column n): X = sum_j J_ij G_j (FP64), column scale, slices
+__global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restrict__ Jtab, const int* __restrict__ nbr,
+                           const int* __restrict__ nbond, int Nr, int Nt, int Nc, int ncol,
+                           __nv_bfloat16* __restrict__ xs, double* __restrict__ tau) {
+  const size_t w = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (w >= (size_t)Nr * ncol) return;
+  const int i = (int)(w / ncol), n = (int)(w % ncol);
+  const int N2 = 2 * Nc;
+  int nb[4], bd[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    nb[q] = nbr[i * 4 + q];
+    bd[q] = nbond[i * 4 + q];
+  }
+  // gather once into registers (Nc <= 256: at most 8 points per lane)
+  constexpr int PER_LANE = 256 / 32;
+  double2 x[PER_LANE];
+  double mx = 0.0;
+#pragma unroll
+  for (int u = 0; u < PER_LANE; ++u) {
+    const int z = lane + 32 * u;
+    double xr = 0.0, xi = 0.0;
+    if (z < Nc) {
+      const int tk = time_of(z, Nt);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (nb[q] < 0) continue;
+        const double Jv = Jtab[(size_t)bd[q] * Nt + tk];
+        const double2 g = G[((size_t)nb[q] * ncol + n) * Nc + z];
+        xr = fma(Jv, g.x, xr);
+        xi = fma(Jv, g.y, xi);
+      }
+    }
+    x[u] = make_double2(xr, xi);
+    mx = fmax(mx, fmax(fabs(xr), fabs(xi)));
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const double sc = pow2_scale(mx);
+  if (lane == 0) tau[w] = sc;
+  const double fix_over_sc = ldexp(1.0, FIX) / sc;
+  const size_t stride = (size_t)Nr * ncol * N2;
+  __nv_bfloat16* dst = xs + w * N2;
+#pragma unroll
+  for (int u = 0; u < PER_LANE; ++u) {
+    const int z = lane + 32 * u;
+    if (z < Nc) {
+      write_slices(x[u].x, fix_over_sc, dst + z, stride);
+      write_slices(x[u].y, fix_over_sc, dst + Nc + z, stride);
+    }
+  }
+}
+
+struct Prod {
+  int s, t, acc;
+};
+__host__ __device__ constexpr Prod prod_of(int p) {
+  // products with s + t <= 7 ordered by diagonal; accumulator min(d - 2, 3)
+  int idx = 0;
+  for (int d = 2; d <= S + 1; ++d)
+    for (int s = 1; s < d; ++s) {
+      int t = d - s;
+      if (s > S || t > S) continue;
+      if (idx == p) return Prod{s, t, d - 2 < NACC - 1 ? d - 2 : NACC - 1};
+      ++idx;
+    }
+  return Prod{0, 0, 0};
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap xmap,
+              const double* __restrict__ sigma, const double* __restrict__ tau, const double2* __restrict__ G,
+              const double2* __restrict__ lam, const int* __restrict__ col_src, int Nc, int ncol,
+              float* __restrict__ r32, unsigned long long* __restrict__ norm, int* __restrict__ err) {
+  using namespace ptx;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = blockIdx.x, nt = blockIdx.y, site = blockIdx.z;
+  const int N2 = 2 * Nc, KB = N2 / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_holder, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_holder;
+  volatile int* abort_p = &abort_flag;
+  auto stage_ptr = [&](int s) { return smem + (size_t)s * STAGE_BYTES; };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % STAGES;
+        if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, abort_p)) break;
+        uint8_t* st = stage_ptr(s);
+        mbar_expect_tx(&full[s], STAGE_BYTES);
+        for (int q = 0; q < S; ++q) {
+          tma_load_4d(st + q * A_TILE, &amap, &full[s], kb * BK, mt * BM, site, q);
+          tma_load_4d(st + S * A_TILE + q * X_TILE, &xmap, &full[s], kb * BK, nt * BN, site, q);
+        }
+        issued = kb + 1;
+      }
+      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+        mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, abort_p, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool any = false;
+      for (int kb = 0; kb < KB; ++kb) {
+        const int s = kb % STAGES;
+        if (!mbar_wait(&full[s], (kb / STAGES) & 1, abort_p)) break;
+        tc_fence_after();
+        const uint32_t base = smem_u32(stage_ptr(s));
+#pragma unroll
+        for (int k16 = 0; k16 < BK / 16; ++k16) {
+#pragma unroll
+          for (int p = 0; p < NPROD; ++p) {
+            constexpr int dummy = 0;
+            (void)dummy;
+            const Prod pr = prod_of(p);
+            const uint64_t ad = sdesc_sw64(base + (pr.s - 1) * A_TILE + k16 * 32);
+            const uint64_t xd = sdesc_sw64(base + S * A_TILE + (pr.t - 1) * X_TILE + k16 * 32);
+            // the first product of each accumulator at the first k step overwrites it
+            const bool first = (kb == 0 && k16 == 0 && (p == 0 || prod_of(p - 1).acc != pr.acc));
+            mma<0>(tmem + (uint32_t)(pr.acc * BN), ad, xd, IDESC, first ? 0u : 1u);
+          }
+        }
+        mma_commit(&empty[s]);
+        any = true;
+      }
+      if (any) {
+        mma_commit(&acc_full);
+        mbar_wait(&acc_full, 0, abort_p, false);
+      }
+    }
+  } else if (warp >= 4) {
+    bool go = mbar_wait(&acc_full, 0, abort_p);
+    go = __all_sync(0xffffffffu, go);
+    if (go) {
+      tc_fence_after();
+      const int q4 = warp - 4;
+      const int m = mt * BM + q4 * 32 + lane;            // planar row: part m / Nc, contour row z = m % Nc
+      const int z = m % Nc, part = m / Nc;
+      const double sg = sigma[(size_t)site * N2 + m] * ldexp(1.0, -FIX);   // row scale / fixed-point unit
+      int qcur = (nt * BN) / Nc;
+      float runmax = 0.f;
+      for (int c = 0; c < BN / 32; ++c) {
+        const int n0 = nt * BN + c * 32;
+        if (n0 >= ncol) break;                          // warp-uniform; ncol is a multiple of 64
+        const int q = n0 / Nc;
+        if (q != qcur) {
+          float mm = runmax;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+          if (lane == 0) atomicMax(norm + qcur, (unsigned long long)__double_as_longlong((double)mm));
+          qcur = q;
+          runmax = 0.f;
+        }
+        // the accumulators hold integer multiples of 2^{-7d}: sum them exactly in
+        // 2^-FIX fixed point (int64), then convert once
+        long long acc[32];
+        uint32_t rr[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0;
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+          tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(a * BN + c * 32), rr);
+          tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[j] += f32_to_fixed(__uint_as_float(rr[j]));
+        }
+        const bool src = (col_src[q] == site);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + j;
+          const double2 g = G[((size_t)site * ncol + n) * Nc + z];
+          double b = 0.0;
+          if (src) {
+            const double2 lv = lam[((size_t)site * Nc + z) * Nc + (n - q * Nc)];
+            b = part ? lv.y : lv.x;
+          }
+          const double rv = b + (double)acc[j] * (sg * tau[(size_t)site * ncol + n]) - (part ? g.y : g.x);
+          r32[((size_t)site * ncol + n) * N2 + m] = (float)rv;
+          float d = fabsf((float)rv);
+          d = (d == d) ? d : __int_as_float(0x7f800000);
+          runmax = fmaxf(runmax, d);
+        }
+      }
+      float mm = runmax;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+      if (lane == 0) atomicMax(norm + qcur, (unsigned long long)__double_as_longlong((double)mm));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 4D bf16 map [d3][d2][d1][d0] with a (32 x rows x 1 x 1) box and 64-byte swizzle
+bool make_map4(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3, uint32_t rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[4] = {d0, d1, d2, d3};
+  cuuint64_t strides[3] = {d0 * 2, d0 * d1 * 2, d0 * d1 * d2 * 2};
+  cuuint32_t box[4] = {(cuuint32_t)BK, rows, 1, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+OzState* state(dyson_ctx* c) {
+  if (!c->oz) c->oz = new OzState();
+  return static_cast<OzState*>(c->oz);
+}
+
+template <class T>
+int grow(dyson_ctx* c, T** p, size_t* have, size_t bytes, const char* what) {
+  if (*have >= bytes) return DYSON_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ctx_fail(c, DYSON_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  *have = bytes;
+  return DYSON_OK;
+}
+
+}  // namespace
+
+// Exactness of the diagonal-5 accumulator needs K = 2Nc <= 2^24 / (3 * 2^13) ~ 682.
+bool oz_supported(dyson_ctx* c) { return c->Nc % 64 == 0 && 2 * c->Nc <= 512 && encode_fn() != nullptr; }
+
+size_t oz_bytes_per_element() { return (size_t)S * 2 * 2; }   // X slices per complex state element
+
+void oz_invalidate(dyson_ctx* c) {
+  if (c->oz) static_cast<OzState*>(c->oz)->a_ready = false;
+}
+
+int oz_residual(dyson_ctx* c, int nq, const double2* G, float* r32) {
+  OzState* st = state(c);
+  const int Nr = c->Nr, Nc = c->Nc, N2 = 2 * Nc, ncol = nq * Nc;
+  int rc;
+  if (!st->d_err) {
+    DY_CUDA(c, cudaMalloc(&st->d_err, sizeof(int)));
+    DY_CUDA(c, cudaMemsetAsync(st->d_err, 0, sizeof(int), c->stream));
+  }
+  if (!st->a_ready) {
+    size_t abytes = (size_t)S * Nr * N2 * N2 * 2;
+    if ((rc = grow(c, &st->aslices, &st->a_bytes, abytes, "Ozaki slices of Lambda"))) return rc;
+    if (!st->sigma) DY_CUDA(c, cudaMalloc(&st->sigma, (size_t)Nr * N2 * sizeof(double)));
+    size_t rows = (size_t)Nr * N2;
+    k_oz_aprep<<<(unsigned)((rows + 7) / 8), 256, 0, c->stream>>>(c->d_lam, Nr, c->Nt, c->Nm, c->dt, c->beta,
+                                                                 st->aslices, st->sigma);
+    c->launches += 1;
+    if (!make_map4(&st->amap, st->aslices, N2, N2, Nr, S, BM))
+      return ctx_fail(c, DYSON_ERR_CUDA, "cuTensorMapEncodeTiled failed for the Lambda slices");
+    st->a_ready = true;
+  }
+  size_t xbytes = (size_t)S * Nr * ncol * N2 * 2;
+  if ((rc = grow(c, &st->xslices, &st->x_bytes, xbytes, "Ozaki slices of X"))) return rc;
+  if ((rc = grow(c, &st->tau, &st->tau_bytes, (size_t)Nr * ncol * sizeof(double), "Ozaki column scales"))) return rc;
+  if (st->xmap_ptr != st->xslices || st->xmap_ncol != ncol) {
+    if (!make_map4(&st->xmap, st->xslices, N2, ncol, Nr, S, BN))
+      return ctx_fail(c, DYSON_ERR_CUDA, "cuTensorMapEncodeTiled failed for the X slices");
+    st->xmap_ptr = st->xslices;
+    st->xmap_ncol = ncol;
+  }
+  if (!st->smem_set) {
+    DY_CUDA(c, cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    st->smem_set = true;
+  }
+  size_t warps = (size_t)Nr * ncol;
+  k_oz_xprep<<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(G, c->dJ, c->d_nbr, c->d_nbond, Nr, c->Nt, Nc,
+                                                                ncol, st->xslices, st->tau);
+  dim3 grid(N2 / BM, (ncol + BN - 1) / BN, Nr);
+  k_oz_gemm<<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
+                                                      c->d_col_src, Nc, ncol, r32, c->d_norm, st->d_err);
+  c->launches += 2;
+  DY_CUDA(c, cudaGetLastError());
+  return DYSON_OK;
+}
+
+int oz_check_error(dyson_ctx* c) {
+  OzState* st = static_cast<OzState*>(c->oz);
+  if (!st || !st->d_err) return DYSON_OK;
+  int h = 0;
+  DY_CUDA(c, cudaMemcpyAsync(&h, st->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (h) {
+    cudaMemsetAsync(st->d_err, 0, sizeof(int), c->stream);
+    return ctx_fail(c, DYSON_ERR_TIMEOUT, "a residual pipeline wait exceeded its time limit");
+  }
+  return DYSON_OK;
+}
+
+void oz_release(dyson_ctx* c) {
+  OzState* st = static_cast<OzState*>(c->oz);
+  if (!st) return;
+  void* ptrs[] = {st->aslices, st->sigma, st->xslices, st->tau, st->d_err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete st;
+  c->oz = nullptr;
+}

@@ -99,7 +99,8 @@ def test_tensor_core_path_matches_dense(torch_cuda, lib, kw):
     s.profile(True)
     got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
     launches, _ = s.profile_query(2)
-    assert launches > 0                                     # the tensor-core kernel ran
+    assert launches > 0                                     # the tensor-core sweep ran
+    assert s.profile_query(4)[0] == res.report["refinements"] > 0   # every residual used BF16 slice products
     for q in range(len(sources)):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
