@@ -28,4 +28,4 @@ adjoint      Gradients of a weighted density sum (no counterpart in the paper;
 Parity status of every function is stated in its docstring; functions whose
 results are not fixed by an independent pin say "parity unpinned".
 """
-from . import contour, lattice, atomic, dyson, observables  # noqa: F401
+from . import contour, lattice, atomic, dyson, observables, adjoint  # noqa: F401
