@@ -131,6 +131,41 @@ int dyson_copy_sigma(dyson_ctx* ctx, double* dst, int on_device);
 int dyson_solve_columns(dyson_ctx* ctx, const int32_t* src_sites, int64_t n_src, int precision,
                         double tol, int32_t max_sweeps, double* g_out, dyson_report* rep);
 
+/* Solve n single vector columns G(:, (s_q, z'_q)): the response to one source site
+ * s_q = sites[q] at one source time z'_q = times[q] (host arrays; 0 <= s < Nr,
+ * 0 <= z' < Nc), the unit-vector right-hand sides of Sec. IV.D.  Same series,
+ * precisions and tolerances as dyson_solve_columns; columns are solved in
+ * groups of 32 (the last group padded with zero columns).  No observables.
+ *   g_out: NULL or a caller-owned DEVICE buffer of n*Nr*Nc complex128 receiving
+ *          G_{j s_q}(z, z'_q) at [q][j][z]. */
+int dyson_solve_vector_columns(dyson_ctx* ctx, const int32_t* sites, const int32_t* times, int64_t n,
+                               int precision, double tol, int32_t max_sweeps, double* g_out,
+                               dyson_report* rep);
+
+/* Transpose every site block Lambda_i in place (call again to undo).  While
+ * transposed, solves return columns of G^T, i.e. rows of G: G^T solves the same
+ * Dyson equation with Lambda_i^T because W and J commute and J is symmetric.
+ * dyson_solve_columns returns DYSON_ERR_STATE in this state (its observables
+ * need columns of G). */
+int dyson_transpose_sigma(dyson_ctx* ctx);
+
+/* Gradients of L = sum_i w_i n_i(t_k), the weighted density per spin at forward
+ * time index t_index (Sec. III.A), with respect to every U_i(t_k) and J_b(t_k)
+ * of the drive tables.  The paper has no gradient; the derivation is
+ *   dG = (I + G W J) dLambda (I + W J G) + G W dJ G,
+ * with the columns G e_i and rows e_i^T G (solved on transposed site blocks, see
+ * dyson_transpose_sigma) at (i, t_index) for every site, and the derivative of
+ * the closed form of Lambda (Sec. III) in U, which includes the dependence of
+ * eps_i and of the Boltzmann weights on U_i(0).
+ *   w       host, [Nr] site weights;
+ *   loss    host, optional: L;
+ *   grad_U  host, optional: [Nr][Nt];  grad_J host, optional: [Nb][Nt].
+ * Solves 2 Nr vector columns with the given precision/tolerance; device memory
+ * 16 (4 Nr^2 Nc + Nr Nc^2) bytes beyond the solves.  Gradients with respect to
+ * scalar drive parameters follow by the chain rule through the tables. */
+int dyson_adjoint(dyson_ctx* ctx, const double* w, int32_t t_index, int precision, double tol,
+                  int32_t max_sweeps, double* loss, double* grad_U, double* grad_J, dyson_report* rep);
+
 /* Observables of the sites solved so far (Sec. III.A, Eq. (docc), App. B):
  * density per spin n_i(t_k), kinetic energy ekin_i(t_k) and double occupancy
  * D_i(t_k), each [Nr][Nt] doubles.  Sites never solved hold NaN; D_i(t_0) is

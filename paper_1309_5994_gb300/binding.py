@@ -51,7 +51,8 @@ class Report(C.Structure):
 
 
 EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_columns",
-           "dyson_observables", "dyson_profile", "dyson_profile_query", "dyson_set_chunk",
+           "dyson_observables", "dyson_solve_vector_columns", "dyson_transpose_sigma", "dyson_adjoint",
+           "dyson_profile", "dyson_profile_query", "dyson_set_chunk",
            "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error"]
 
@@ -72,6 +73,10 @@ def load(path: str = _LIB_PATH):
     lib.dyson_solve_columns.argtypes = [P, C.POINTER(C.c_int32), C.c_int64, C.c_int, C.c_double, C.c_int32, P,
                                         C.POINTER(Report)]
     lib.dyson_observables.argtypes = [P, P, P, P, C.c_int]
+    lib.dyson_solve_vector_columns.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int64, C.c_int,
+                                               C.c_double, C.c_int32, P, C.POINTER(Report)]
+    lib.dyson_transpose_sigma.argtypes = [P]
+    lib.dyson_adjoint.argtypes = [P, P, C.c_int32, C.c_int, C.c_double, C.c_int32, P, P, P, C.POINTER(Report)]
     lib.dyson_profile.argtypes = [P, C.c_int]
     lib.dyson_profile_query.argtypes = [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     lib.dyson_set_chunk.argtypes = [P, C.c_int32]
@@ -158,6 +163,41 @@ class Solver:
                                           tol, max_sweeps, gptr, C.byref(rep))
         self._check(rc, ok=allow)
         return SolveResult(rc, rep.as_dict())
+
+    def solve_vectors(self, sites, times, precision=PREC_F64, tol=1e-13, max_sweeps=400, g_out=None, allow=(0,)):
+        """Solve vector columns (sites[q], times[q]); g_out: optional complex128 device
+        tensor of shape [n, Nr, Nc].  Returns SolveResult."""
+        s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
+        t = np.ascontiguousarray(np.asarray(times, dtype=np.int32))
+        assert s.shape == t.shape
+        rep = Report()
+        gptr = None
+        if g_out is not None:
+            assert g_out.is_cuda and g_out.dtype == self._torch.complex128 and g_out.is_contiguous()
+            assert g_out.numel() == len(s) * self.p.Nr * self.p.Nc
+            gptr = C.c_void_p(g_out.data_ptr())
+        rc = self.lib.dyson_solve_vector_columns(self.h, s.ctypes.data_as(C.POINTER(C.c_int32)),
+                                                 t.ctypes.data_as(C.POINTER(C.c_int32)), len(s), precision, tol,
+                                                 max_sweeps, gptr, C.byref(rep))
+        self._check(rc, ok=allow)
+        return SolveResult(rc, rep.as_dict())
+
+    def adjoint(self, w, t_index=None, precision=PREC_TF32X3_F64REF, tol=1e-11, max_sweeps=400, allow=(0,)):
+        """(loss, dL/dU [Nr, Nt], dL/dJ [Nb, Nt], SolveResult) of L = sum_i w_i n_i(t_index)."""
+        t_index = self.p.Nt - 1 if t_index is None else t_index
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        assert w.shape == (self.p.Nr,)
+        loss = C.c_double()
+        gU = np.zeros((self.p.Nr, self.p.Nt))
+        gJ = np.zeros((max(self.p.Nb, 1), self.p.Nt))
+        rep = Report()
+        rc = self.lib.dyson_adjoint(self.h, w.ctypes.data, t_index, precision, tol, max_sweeps, C.byref(loss),
+                                    gU.ctypes.data, gJ.ctypes.data, C.byref(rep))
+        self._check(rc, ok=allow)
+        return loss.value, gU, gJ[:self.p.Nb], SolveResult(rc, rep.as_dict())
+
+    def transpose_sigma(self):
+        self._check(self.lib.dyson_transpose_sigma(self.h))
 
     def observables(self):
         """(n, ekin, D) as host numpy arrays [Nr, Nt]."""

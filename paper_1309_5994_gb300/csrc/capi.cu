@@ -88,38 +88,52 @@ int ensure_work(dyson_ctx* c, size_t bytes) {
   return DYSON_OK;
 }
 
-int ensure_cols(dyson_ctx* c, int nq) {
-  if (c->col_src_cap < nq) {
-    if (c->d_col_src) cudaFree(c->d_col_src);
-    c->d_col_src = nullptr;
-    DY_CUDA(c, dalloc(&c->d_col_src, nq));
-    c->col_src_cap = nq;
+// per-vector-column source arrays (ncol entries) and per-group norm/scale words (ng groups)
+int ensure_cols(dyson_ctx* c, int ncol, int ng) {
+  if (c->src_cap < ncol) {
+    if (c->d_src_site) cudaFree(c->d_src_site);
+    if (c->d_src_time) cudaFree(c->d_src_time);
+    c->d_src_site = c->d_src_time = nullptr;
+    c->src_cap = 0;
+    DY_CUDA(c, dalloc(&c->d_src_site, ncol));
+    DY_CUDA(c, dalloc(&c->d_src_time, ncol));
+    c->src_cap = ncol;
   }
-  if (c->norm_cap < nq) {
+  if (c->norm_cap < ng) {
     if (c->d_norm) cudaFree(c->d_norm);
     if (c->h_norm) cudaFreeHost(c->h_norm);
     c->d_norm = nullptr;
     c->h_norm = nullptr;
-    DY_CUDA(c, dalloc(&c->d_norm, 2 * (size_t)nq));
-    DY_CUDA(c, cudaMallocHost((void**)&c->h_norm, 2 * (size_t)nq * sizeof(unsigned long long)));
-    c->norm_cap = nq;
+    c->norm_cap = 0;
+    DY_CUDA(c, dalloc(&c->d_norm, 2 * (size_t)ng));
+    DY_CUDA(c, cudaMallocHost((void**)&c->h_norm, 2 * (size_t)ng * sizeof(unsigned long long)));
+    c->norm_cap = ng;
   }
   return DYSON_OK;
 }
 
-// read norm[0..nq) (and scale[nq..2nq) when with_scale) to the host
-int read_norms(dyson_ctx* c, int nq, bool with_scale) {
-  DY_CUDA(c, cudaMemcpyAsync(c->h_norm, c->d_norm, (with_scale ? 2 : 1) * (size_t)nq * sizeof(unsigned long long),
+// copy the host source arrays of the current chunk to the device
+int upload_sources(dyson_ctx* c, int ncol) {
+  DY_CUDA(c, cudaMemcpyAsync(c->d_src_site, c->h_src_site.data(), ncol * sizeof(int), cudaMemcpyHostToDevice,
+                             c->stream));
+  DY_CUDA(c, cudaMemcpyAsync(c->d_src_time, c->h_src_time.data(), ncol * sizeof(int), cudaMemcpyHostToDevice,
+                             c->stream));
+  return DYSON_OK;
+}
+
+// read norm[0..ng) (and scale[ng..2ng) when with_scale) to the host
+int read_norms(dyson_ctx* c, int ng, bool with_scale) {
+  DY_CUDA(c, cudaMemcpyAsync(c->h_norm, c->d_norm, (with_scale ? 2 : 1) * (size_t)ng * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, c->stream));
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
   flush_timers(c);
   return DYSON_OK;
 }
 
-// max over block columns of norm[q] / ref[q]
-double rel_max(const unsigned long long* norm, const double* ref, int nq) {
+// max over groups of norm[q] / ref[q] (groups with ref = 0 hold only padding columns)
+double rel_max(const unsigned long long* norm, const double* ref, int ng) {
   double m = 0.0;
-  for (int q = 0; q < nq; ++q) {
+  for (int q = 0; q < ng; ++q) {
     double v = bits_to_double(norm[q]) / std::max(ref[q], 1e-300);
     if (!(v == v)) return std::numeric_limits<double>::infinity();
     m = std::max(m, v);
@@ -129,34 +143,39 @@ double rel_max(const unsigned long long* norm, const double* ref, int nq) {
 
 constexpr double kDivergedGrowth = 1e200;
 
-// plain FP64 series: G <- B + K G until the relative update <= tol
-int solve_f64(dyson_ctx* c, int nq, double tol, int max_sweeps, double2** result, dyson_report* r) {
-  const size_t ncol = (size_t)nq * c->Nc, n_el = (size_t)c->Nr * ncol * c->Nc;
+// algorithmic contour-GEMM flops of one sweep over ncol vector columns
+double sweep_flops(const dyson_ctx* c, int ncol) { return 8.0 * c->Nc * (double)c->Nc * c->Nr * ncol; }
+
+// Plain FP64 series over the chunk (ncol vector columns, norm groups of gs columns):
+// G <- B + K G until the relative update <= tol
+int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double2** result, dyson_report* r) {
+  const int ng = ncol / gs;
+  const size_t n_el = (size_t)c->Nr * ncol * c->Nc;
   double2* Ga = (double2*)c->work;
   double2* Gb = Ga + n_el;
   DY_CUDA(c, cudaMemsetAsync(Ga, 0, n_el * sizeof(double2), c->stream));
-  DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, 2 * (size_t)nq * sizeof(unsigned long long), c->stream));
-  launch_init_rhs(c->d_lam, c->d_col_src, c->Nr, c->Nc, (int)ncol, Ga, c->d_norm + nq, c->stream);
+  DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, 2 * (size_t)ng * sizeof(unsigned long long), c->stream));
+  launch_init_rhs(c->d_lam, c->d_src_site, c->d_src_time, c->Nr, c->Nc, ncol, gs, Ga, c->d_norm + ng, c->stream);
   c->launches += 1;
-  int rc = read_norms(c, nq, true);
+  int rc = read_norms(c, ng, true);
   if (rc) return rc;
-  std::vector<double> scale(nq);
-  for (int q = 0; q < nq; ++q) scale[q] = bits_to_double(c->h_norm[nq + q]);
+  std::vector<double> scale(ng);
+  for (int q = 0; q < ng; ++q) scale[q] = bits_to_double(c->h_norm[ng + q]);
   int status = DYSON_ERR_NOT_CONVERGED;
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
-    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)nq * sizeof(unsigned long long), c->stream));
+    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
     {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F64);
-      launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, Ga, Gb, nullptr, c->d_col_src, c->Nr, c->Nc,
-                       (int)ncol, 0, c->d_norm, c->stream);
+      launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, Ga, Gb, nullptr, c->d_src_site, c->d_src_time,
+                       c->Nr, c->Nc, ncol, gs, 0, c->d_norm, c->stream);
       c->launches += 1;
     }
     DY_CUDA(c, cudaGetLastError());
-    if ((rc = read_norms(c, nq, false))) return rc;
+    if ((rc = read_norms(c, ng, false))) return rc;
     std::swap(Ga, Gb);
-    double upd = rel_max(c->h_norm, scale.data(), nq);
+    double upd = rel_max(c->h_norm, scale.data(), ng);
     r->sweeps += 1;
-    r->gemm_flops += 8.0 * c->Nc * (double)c->Nc * c->Nc * c->Nr * nq;
+    r->gemm_flops += sweep_flops(c, ncol);
     r->update = upd;
     if (!(upd < kDivergedGrowth)) {
       status = DYSON_ERR_DIVERGED;
@@ -172,30 +191,31 @@ int solve_f64(dyson_ctx* c, int nq, double tol, int max_sweeps, double2** result
 }
 
 // inner solve d <- r + K d in FP32 (SIMT or 3xTF32 tensor cores)
-int inner_solve(dyson_ctx* c, int nq, int precision, float* r32, float* da, float* db, int max_sweeps,
+int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float* da, float* db, int max_sweeps,
                 const std::vector<double>& rref, float** dres, dyson_report* rep) {
-  const size_t ncol = (size_t)nq * c->Nc, n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
+  const int ng = ncol / gs;
+  const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
   DY_CUDA(c, cudaMemcpyAsync(da, r32, n32 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
   double best = std::numeric_limits<double>::infinity(), peak = 0.0;
   int since_best = 0, rc;
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
-    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)nq * sizeof(unsigned long long), c->stream));
+    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
     if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_TC);
-      if ((rc = tc_sweep(c, nq, r32, da, db))) return rc;
+      if ((rc = tc_sweep(c, ncol, gs, r32, da, db))) return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
-      launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, (int)ncol,
+      launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, ncol, gs,
                             c->d_norm, c->stream);
       c->launches += 1;
     }
     DY_CUDA(c, cudaGetLastError());
-    if ((rc = read_norms(c, nq, false))) return rc;
+    if ((rc = read_norms(c, ng, false))) return rc;
     if (c->use_tc && (rc = tc_check_error(c))) return rc;
     std::swap(da, db);
-    double upd = rel_max(c->h_norm, rref.data(), nq);
+    double upd = rel_max(c->h_norm, rref.data(), ng);
     rep->sweeps += 1;
-    rep->gemm_flops += 8.0 * c->Nc * (double)c->Nc * c->Nc * c->Nr * nq;
+    rep->gemm_flops += sweep_flops(c, ncol);
     rep->update = upd;
     if (!(upd < kDivergedGrowth)) return ctx_fail(c, DYSON_ERR_DIVERGED, "FP32 series update not finite");
     // The update first grows (transient of the real-time series), falls
@@ -217,48 +237,49 @@ int inner_solve(dyson_ctx* c, int nq, int precision, float* r32, float* da, floa
 }
 
 // complex FP32 series refined by FP64 residuals: G += solve(r), r = B + K G - G
-int solve_mixed(dyson_ctx* c, int nq, int precision, double tol, int max_sweeps, double2** result,
+int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int max_sweeps, double2** result,
                 dyson_report* rep) {
-  const size_t ncol = (size_t)nq * c->Nc, n_el = (size_t)c->Nr * ncol * c->Nc;
+  const int ng = ncol / gs;
+  const size_t n_el = (size_t)c->Nr * ncol * c->Nc;
   double2* G = (double2*)c->work;
   float* r32 = (float*)(G + n_el);
   float* da = r32 + 2 * n_el;
   float* db = da + 2 * n_el;
   int rc;
-  // r = B (FP32), scale = max |Lambda_s|; G = 0
+  // r = B (FP32), scale = max |B| per group; G = 0
   DY_CUDA(c, cudaMemsetAsync(G, 0, n_el * sizeof(double2), c->stream));
-  DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, 2 * (size_t)nq * sizeof(unsigned long long), c->stream));
-  launch_init_rhs(c->d_lam, c->d_col_src, c->Nr, c->Nc, (int)ncol, G, c->d_norm + nq, c->stream);
+  DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, 2 * (size_t)ng * sizeof(unsigned long long), c->stream));
+  launch_init_rhs(c->d_lam, c->d_src_site, c->d_src_time, c->Nr, c->Nc, ncol, gs, G, c->d_norm + ng, c->stream);
   launch_to_planar32(G, r32, n_el, c->Nc, c->stream);
   c->launches += 2;
   DY_CUDA(c, cudaMemsetAsync(G, 0, n_el * sizeof(double2), c->stream));
-  if ((rc = read_norms(c, nq, true))) return rc;
-  std::vector<double> scale(nq), rref(nq);
-  for (int q = 0; q < nq; ++q) rref[q] = scale[q] = bits_to_double(c->h_norm[nq + q]);
+  if ((rc = read_norms(c, ng, true))) return rc;
+  std::vector<double> scale(ng), rref(ng);
+  for (int q = 0; q < ng; ++q) rref[q] = scale[q] = bits_to_double(c->h_norm[ng + q]);
   int status = DYSON_ERR_NOT_CONVERGED;
   for (int ref = 0; ref < c->max_refinements; ++ref) {
     float* d = nullptr;
-    if ((rc = inner_solve(c, nq, precision, r32, da, db, max_sweeps, rref, &d, rep))) return rc;
-    launch_accumulate(G, d, c->Nr, c->Nc, (int)ncol, c->stream);
+    if ((rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep))) return rc;
+    launch_accumulate(G, d, c->Nr, c->Nc, ncol, c->stream);
     c->launches += 1;
-    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)nq * sizeof(unsigned long long), c->stream));
+    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
     if (c->use_oz) {
       KernelTimer t(c, DYSON_KERNEL_RESIDUAL_SPLIT);
-      if ((rc = oz_residual(c, nq, G, r32))) return rc;
+      if ((rc = oz_residual(c, ncol, gs, G, r32))) return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_RESIDUAL_F64);
-      launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, G, nullptr, r32, c->d_col_src, c->Nr, c->Nc,
-                       (int)ncol, 1, c->d_norm, c->stream);
+      launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, G, nullptr, r32, c->d_src_site, c->d_src_time,
+                       c->Nr, c->Nc, ncol, gs, 1, c->d_norm, c->stream);
       c->launches += 1;
     }
     DY_CUDA(c, cudaGetLastError());
-    if ((rc = read_norms(c, nq, false))) return rc;
+    if ((rc = read_norms(c, ng, false))) return rc;
     if (c->use_oz && (rc = oz_check_error(c))) return rc;
     rep->refinements += 1;
-    rep->gemm_flops += 8.0 * c->Nc * (double)c->Nc * c->Nc * c->Nr * nq;
-    double res = rel_max(c->h_norm, scale.data(), nq);
+    rep->gemm_flops += sweep_flops(c, ncol);
+    double res = rel_max(c->h_norm, scale.data(), ng);
     rep->residual = res;
-    for (int q = 0; q < nq; ++q) rref[q] = std::max(bits_to_double(c->h_norm[q]), 1e-300);
+    for (int q = 0; q < ng; ++q) rref[q] = std::max(bits_to_double(c->h_norm[q]), 1e-300);
     if (!(res < kDivergedGrowth)) {
       status = DYSON_ERR_DIVERGED;
       break;
@@ -396,79 +417,138 @@ int dyson_copy_sigma(dyson_ctx* c, double* dst, int on_device) {
   return DYSON_OK;
 }
 
-int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
-                        int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
-  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
-  dyson_report rep;
-  std::memset(&rep, 0, sizeof rep);
-  auto t0 = std::chrono::steady_clock::now();
-  const int64_t launches0 = c->launches;
-  auto finish = [&](int code) {
-    rep.status = code;
-    rep.kernel_launches = c->launches - launches0;
-    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    if (rep_out) *rep_out = rep;
-    return code;
-  };
-  if (!c->sigma_built) return finish(ctx_fail(c, DYSON_ERR_STATE, "dyson_build_sigma has not run"));
-  if (n_src < 1 || !src) return finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "need at least one source site"));
-  for (int64_t q = 0; q < n_src; ++q)
-    if (src[q] < 0 || src[q] >= c->Nr) return finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "source site out of range"));
-  if (precision != DYSON_PREC_F64 && precision != DYSON_PREC_TF32X3_F64REF)
-    return finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "unknown precision"));
-  if (!(tol > 0) || max_sweeps < 1) return finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "need tol > 0 and max_sweeps >= 1"));
-  DeviceGuard g(c->device);
-  int rc;
-  if (precision != DYSON_PREC_F64) {
-    if (!c->lam32_built && (!c->tc_enabled || !tc_supported(c, c->Nc))) {
-      if (!c->d_lam32) DY_CUDA(c, dalloc(&c->d_lam32, (size_t)c->Nr * c->Nc * c->Nc));
-      launch_lam_c64(c->d_lam, c->Nr, c->Nt, c->Nm, c->dt, c->beta, c->d_lam32, c->stream);
-      c->launches += 1;
-      c->lam32_built = true;
-    }
-    if (c->tc_enabled && tc_supported(c, c->Nc) && !c->lam_split_built) {
-      size_t n = (size_t)c->Nr * 4 * c->Nc * c->Nc;
-      if (!c->d_lam_hi) DY_CUDA(c, dalloc(&c->d_lam_hi, n));
-      if (!c->d_lam_lo) DY_CUDA(c, dalloc(&c->d_lam_lo, n));
-      launch_lam_emb_split(c->d_lam, c->Nr, c->Nt, c->Nm, c->dt, c->beta, c->d_lam_hi, c->d_lam_lo, c->stream);
-      c->launches += 1;
-      c->lam_split_built = true;
-    }
-    c->use_tc = c->tc_enabled && tc_supported(c, c->Nc);
-    if (!c->use_tc && !c->lam32_built) return finish(ctx_fail(c, DYSON_ERR_STATE, "FP32 tables missing"));
+}  // extern "C"
+
+namespace {
+
+// Build the reduced-precision copies of Lambda a solve needs and pick the sweep
+// and residual kernels (sets c->use_tc, c->use_oz).
+int prepare_tables(dyson_ctx* c, int precision) {
+  c->use_tc = c->use_oz = false;
+  if (precision == DYSON_PREC_F64) return DYSON_OK;
+  const bool tc = c->tc_enabled && tc_supported(c, c->Nc);
+  if (!tc && !c->lam32_built) {
+    if (!c->d_lam32) DY_CUDA(c, dalloc(&c->d_lam32, (size_t)c->Nr * c->Nc * c->Nc));
+    launch_lam_c64(c->d_lam, c->Nr, c->Nt, c->Nm, c->dt, c->beta, c->d_lam32, c->stream);
+    c->launches += 1;
+    c->lam32_built = true;
   }
-  // chunk size from free device memory (bytes per block column of work state)
-  // F64: two complex128 states; mixed: complex128 G + three FP32 states (+ the
-  // FP32 gather buffer of the tensor-core sweep)
-  c->use_oz = precision != DYSON_PREC_F64 && c->use_tc && c->oz_enabled && oz_supported(c);
+  if (tc && !c->lam_split_built) {
+    size_t n = (size_t)c->Nr * 4 * c->Nc * c->Nc;
+    if (!c->d_lam_hi) DY_CUDA(c, dalloc(&c->d_lam_hi, n));
+    if (!c->d_lam_lo) DY_CUDA(c, dalloc(&c->d_lam_lo, n));
+    launch_lam_emb_split(c->d_lam, c->Nr, c->Nt, c->Nm, c->dt, c->beta, c->d_lam_hi, c->d_lam_lo, c->stream);
+    c->launches += 1;
+    c->lam_split_built = true;
+  }
+  c->use_tc = tc;
+  c->use_oz = tc && c->oz_enabled && oz_supported(c);
+  return DYSON_OK;
+}
+
+// Largest number of vector columns, a multiple of `unit` and at most `want`, whose
+// work state fits in 85 % of the free device memory.  F64: two complex128 states;
+// mixed: complex128 G + three FP32 states (+ the FP32 gather buffer of the
+// tensor-core sweep, + the BF16 slices of the split-product residual).
+int64_t chunk_columns(dyson_ctx* c, int precision, int64_t unit, int64_t want, size_t* bytes_per_col) {
   const double per_el = precision == DYSON_PREC_F64
                             ? 32.0
                             : (c->use_tc ? 48.0 : 40.0) + (c->use_oz ? (double)oz_bytes_per_element() : 0.0);
-  const double col_bytes = per_el * c->Nr * (double)c->Nc * c->Nc;
+  const double col_bytes = per_el * c->Nr * (double)c->Nc;
+  *bytes_per_col = (size_t)col_bytes;
   size_t free_b = 0, total_b = 0;
-  DY_CUDA(c, cudaMemGetInfo(&free_b, &total_b));
-  double budget = 0.85 * (double)(free_b + c->work_bytes);
-  int64_t chunk = (int64_t)(budget / col_bytes);
-  if (const char* e = std::getenv("DYSON_CHUNK")) chunk = std::min<int64_t>(chunk, std::max(1, atoi(e)));
-  if (c->chunk_override > 0) chunk = std::min<int64_t>(chunk, c->chunk_override);
-  chunk = std::min<int64_t>(std::min<int64_t>(chunk, n_src), 65535);
-  if (chunk < 1) return finish(ctx_fail(c, DYSON_ERR_OOM, "one block column does not fit in device memory"));
-  if ((rc = ensure_work(c, (size_t)(chunk * col_bytes)))) return finish(rc);
-  if ((rc = ensure_cols(c, (int)chunk))) return finish(rc);
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
+  const double budget = 0.85 * (double)(free_b + c->work_bytes);
+  int64_t cols = (int64_t)(budget / col_bytes);
+  if (const char* e = std::getenv("DYSON_CHUNK")) cols = std::min<int64_t>(cols, (int64_t)std::max(1, atoi(e)) * unit);
+  if (c->chunk_override > 0) cols = std::min<int64_t>(cols, (int64_t)c->chunk_override * unit);
+  cols = std::min<int64_t>(cols, want);
+  cols = std::min<int64_t>(cols, (int64_t)1 << 24);
+  return (cols / unit) * unit;
+}
+
+int solve_chunk(dyson_ctx* c, int ncol, int gs, int precision, double tol, int max_sweeps, double2** G,
+                dyson_report* rep) {
+  int rc = upload_sources(c, ncol);
+  if (rc) return rc;
+  return precision == DYSON_PREC_F64 ? solve_f64(c, ncol, gs, tol, max_sweeps, G, rep)
+                                     : solve_mixed(c, ncol, gs, precision, tol, max_sweeps, G, rep);
+}
+
+int check_solve_args(dyson_ctx* c, int precision, double tol, int max_sweeps) {
+  if (!c->sigma_built) return ctx_fail(c, DYSON_ERR_STATE, "dyson_build_sigma has not run");
+  if (precision != DYSON_PREC_F64 && precision != DYSON_PREC_TF32X3_F64REF)
+    return ctx_fail(c, DYSON_ERR_INVALID_ARG, "unknown precision");
+  if (!(tol > 0) || max_sweeps < 1) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "need tol > 0 and max_sweeps >= 1");
+  return DYSON_OK;
+}
+
+struct ReportScope {
+  dyson_ctx* c;
+  dyson_report rep;
+  dyson_report* out;
+  int64_t launches0;
+  std::chrono::steady_clock::time_point t0;
+  ReportScope(dyson_ctx* cc, dyson_report* o) : c(cc), out(o), launches0(cc->launches) {
+    std::memset(&rep, 0, sizeof rep);
+    t0 = std::chrono::steady_clock::now();
+  }
+  int finish(int code) {
+    rep.status = code;
+    rep.kernel_launches = c->launches - launches0;
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (out) *out = rep;
+    return code;
+  }
+};
+
+int fold_status(int status, int st) {
+  if (st != DYSON_OK && status == DYSON_OK) return st;
+  return status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
+                        int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  ReportScope R(c, rep_out);
+  int rc = check_solve_args(c, precision, tol, max_sweeps);
+  if (rc) return R.finish(rc);
+  if (c->sigma_transposed)
+    return R.finish(ctx_fail(c, DYSON_ERR_STATE, "Lambda is transposed: block columns and observables need it upright"));
+  if (n_src < 1 || !src) return R.finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "need at least one source site"));
+  for (int64_t q = 0; q < n_src; ++q)
+    if (src[q] < 0 || src[q] >= c->Nr) return R.finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "source site out of range"));
+  DeviceGuard g(c->device);
+  if ((rc = prepare_tables(c, precision))) return R.finish(rc);
+  size_t col_bytes = 0;
+  const int64_t cols = chunk_columns(c, precision, c->Nc, n_src * (int64_t)c->Nc, &col_bytes);
+  if (cols < c->Nc) return R.finish(ctx_fail(c, DYSON_ERR_OOM, "one block column does not fit in device memory"));
+  const int64_t chunk = cols / c->Nc;
+  if ((rc = ensure_work(c, (size_t)cols * col_bytes))) return R.finish(rc);
+  if ((rc = ensure_cols(c, (int)cols, (int)chunk))) return R.finish(rc);
 
   int status = DYSON_OK;
   for (int64_t start = 0; start < n_src; start += chunk) {
-    int nq = (int)std::min<int64_t>(chunk, n_src - start);
-    size_t ncol = (size_t)nq * c->Nc;
-    DY_CUDA(c, cudaMemcpyAsync(c->d_col_src, src + start, nq * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream));
+    const int nq = (int)std::min<int64_t>(chunk, n_src - start);
+    const int ncol = nq * c->Nc;
+    c->h_src_site.resize(ncol);
+    c->h_src_time.resize(ncol);
+    for (int q = 0; q < nq; ++q)
+      for (int z = 0; z < c->Nc; ++z) {
+        c->h_src_site[q * c->Nc + z] = src[start + q];
+        c->h_src_time[q * c->Nc + z] = z;
+      }
     double2* G = nullptr;
-    int st = precision == DYSON_PREC_F64 ? solve_f64(c, nq, tol, max_sweeps, &G, &rep)
-                                         : solve_mixed(c, nq, precision, tol, max_sweeps, &G, &rep);
-    if (st != DYSON_OK && st != DYSON_ERR_NOT_CONVERGED && st != DYSON_ERR_DIVERGED) return finish(st);
-    if (st != DYSON_OK && status == DYSON_OK) status = st;
-    rep.chunks += 1;
-    launch_observables(G, c->d_col_src, nq, c->d_nbr, c->d_nbond, c->dJ, c->d_eps, c->dU, c->Nr, c->Nt, c->Nc,
-                       (int)ncol, c->dt, c->d_obs, c->stream);
+    int st = solve_chunk(c, ncol, c->Nc, precision, tol, max_sweeps, &G, &R.rep);
+    if (st != DYSON_OK && st != DYSON_ERR_NOT_CONVERGED && st != DYSON_ERR_DIVERGED) return R.finish(st);
+    status = fold_status(status, st);
+    R.rep.chunks += 1;
+    launch_observables(G, c->d_src_site, nq, c->d_nbr, c->d_nbond, c->dJ, c->d_eps, c->dU, c->Nr, c->Nt, c->Nc,
+                       ncol, c->dt, c->d_obs, c->stream);
     c->launches += 1;
     if (g_out) {
       launch_export(G, c->Nr, c->Nc, nq, (double2*)g_out + (size_t)start * c->Nr * c->Nc * c->Nc, c->stream);
@@ -480,7 +560,133 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
   flush_timers(c);
   if (status == DYSON_ERR_NOT_CONVERGED) ctx_fail(c, status, "max_sweeps or refinement limit reached above tolerance");
   if (status == DYSON_ERR_DIVERGED) ctx_fail(c, status, "series diverged (update not finite or above 1e200)");
-  return finish(status);
+  return R.finish(status);
+}
+
+int dyson_solve_vector_columns(dyson_ctx* c, const int32_t* sites, const int32_t* times, int64_t n, int precision,
+                               double tol, int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  ReportScope R(c, rep_out);
+  int rc = check_solve_args(c, precision, tol, max_sweeps);
+  if (rc) return R.finish(rc);
+  if (n < 1 || !sites || !times) return R.finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "need at least one column"));
+  for (int64_t q = 0; q < n; ++q)
+    if (sites[q] < 0 || sites[q] >= c->Nr || times[q] < 0 || times[q] >= c->Nc)
+      return R.finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "column source out of range"));
+  DeviceGuard g(c->device);
+  if ((rc = prepare_tables(c, precision))) return R.finish(rc);
+  constexpr int GS = 32;                                   // norm group; columns padded to a multiple
+  const int64_t padded = (n + GS - 1) / GS * GS;
+  size_t col_bytes = 0;
+  const int64_t chunk = chunk_columns(c, precision, GS, padded, &col_bytes);
+  if (chunk < GS) return R.finish(ctx_fail(c, DYSON_ERR_OOM, "32 vector columns do not fit in device memory"));
+  if ((rc = ensure_work(c, (size_t)chunk * col_bytes))) return R.finish(rc);
+  if ((rc = ensure_cols(c, (int)chunk, (int)(chunk / GS)))) return R.finish(rc);
+  int status = DYSON_OK;
+  for (int64_t start = 0; start < padded; start += chunk) {
+    const int ncol = (int)std::min<int64_t>(chunk, padded - start);
+    c->h_src_site.assign(ncol, -1);
+    c->h_src_time.assign(ncol, 0);
+    const int nv = (int)std::min<int64_t>(ncol, n - start);
+    for (int k = 0; k < nv; ++k) {
+      c->h_src_site[k] = sites[start + k];
+      c->h_src_time[k] = times[start + k];
+    }
+    double2* G = nullptr;
+    int st = solve_chunk(c, ncol, GS, precision, tol, max_sweeps, &G, &R.rep);
+    if (st != DYSON_OK && st != DYSON_ERR_NOT_CONVERGED && st != DYSON_ERR_DIVERGED) return R.finish(st);
+    status = fold_status(status, st);
+    R.rep.chunks += 1;
+    if (g_out) {
+      launch_export_vectors(G, c->Nr, c->Nc, ncol, nv, (double2*)g_out + (size_t)start * c->Nr * c->Nc, c->stream);
+      c->launches += 1;
+    }
+    DY_CUDA(c, cudaGetLastError());
+  }
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  flush_timers(c);
+  if (status == DYSON_ERR_NOT_CONVERGED) ctx_fail(c, status, "max_sweeps or refinement limit reached above tolerance");
+  if (status == DYSON_ERR_DIVERGED) ctx_fail(c, status, "series diverged (update not finite or above 1e200)");
+  return R.finish(status);
+}
+
+int dyson_adjoint(dyson_ctx* c, const double* w, int32_t t_index, int precision, double tol, int32_t max_sweeps,
+                  double* loss, double* grad_U, double* grad_J, dyson_report* rep_out) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  ReportScope R(c, rep_out);
+  int rc = check_solve_args(c, precision, tol, max_sweeps);
+  if (rc) return R.finish(rc);
+  if (c->sigma_transposed) return R.finish(ctx_fail(c, DYSON_ERR_STATE, "Lambda is transposed"));
+  if (!w || t_index < 0 || t_index >= c->Nt) return R.finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "bad weights or time"));
+  DeviceGuard g(c->device);
+  const int Nr = c->Nr, Nc = c->Nc, Nt = c->Nt;
+  const size_t colbuf = (size_t)Nr * Nr * Nc;                 // double2 elements of C (and R, gamma, rho)
+  const size_t need = (4 * colbuf + (size_t)Nr * Nc * Nc) * sizeof(double2) +
+                      ((size_t)Nr + 1 + (size_t)Nr * Nt + (size_t)std::max(c->Nb, 1) * Nt) * sizeof(double);
+  if (c->adj_bytes < need) {
+    if (c->adj) cudaFree(c->adj);
+    c->adj = nullptr;
+    c->adj_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->adj, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return R.finish(ctx_fail(c, DYSON_ERR_OOM, "adjoint buffers"));
+    }
+    c->adj_bytes = need;
+  }
+  double2* C = (double2*)c->adj;
+  double2* Rw = C + colbuf;
+  double2* gam = Rw + colbuf;
+  double2* rho = gam + colbuf;
+  double2* M = rho + colbuf;
+  double* w_dev = (double*)(M + (size_t)Nr * Nc * Nc);
+  double* loss_dev = w_dev + Nr;
+  double* gU_dev = loss_dev + 1;
+  double* gJ_dev = gU_dev + (size_t)Nr * Nt;
+  DY_CUDA(c, cudaMemcpyAsync(w_dev, w, Nr * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  std::vector<int32_t> sites(Nr), times(Nr, t_index);
+  for (int i = 0; i < Nr; ++i) sites[i] = i;
+  // columns G e_i and rows e_i^T G (columns of G^T) at (i, t_index) for every site
+  dyson_report r1, r2;
+  int st1 = dyson_solve_vector_columns(c, sites.data(), times.data(), Nr, precision, tol, max_sweeps,
+                                       (double*)C, &r1);
+  if (st1 != DYSON_OK && st1 != DYSON_ERR_NOT_CONVERGED) return R.finish(st1);
+  if ((rc = dyson_transpose_sigma(c))) return R.finish(rc);
+  int st2 = dyson_solve_vector_columns(c, sites.data(), times.data(), Nr, precision, tol, max_sweeps,
+                                       (double*)Rw, &r2);
+  if ((rc = dyson_transpose_sigma(c))) return R.finish(rc);
+  if (st2 != DYSON_OK && st2 != DYSON_ERR_NOT_CONVERGED) return R.finish(st2);
+  R.rep.sweeps = r1.sweeps + r2.sweeps;
+  R.rep.refinements = r1.refinements + r2.refinements;
+  R.rep.chunks = r1.chunks + r2.chunks;
+  R.rep.gemm_flops = r1.gemm_flops + r2.gemm_flops;
+  R.rep.update = std::max(r1.update, r2.update);
+  R.rep.residual = std::max(r1.residual, r2.residual);
+  if ((rc = adjoint_contract(c, C, Rw, w_dev, t_index, gam, rho, M, loss_dev, gU_dev, gJ_dev))) return R.finish(rc);
+  if (loss) DY_CUDA(c, cudaMemcpyAsync(loss, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (grad_U)
+    DY_CUDA(c, cudaMemcpyAsync(grad_U, gU_dev, (size_t)Nr * Nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (grad_J && c->Nb > 0)
+    DY_CUDA(c, cudaMemcpyAsync(grad_J, gJ_dev, (size_t)c->Nb * Nt * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int status = fold_status(st1, st2);
+  if (status == DYSON_ERR_NOT_CONVERGED) ctx_fail(c, status, "max_sweeps or refinement limit reached above tolerance");
+  return R.finish(status);
+}
+
+int dyson_transpose_sigma(dyson_ctx* c) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (!c->sigma_built) return ctx_fail(c, DYSON_ERR_STATE, "dyson_build_sigma has not run");
+  DeviceGuard g(c->device);
+  launch_transpose_blocks(c->d_lam, c->Nr, c->Nc, c->stream);
+  c->launches += 1;
+  DY_CUDA(c, cudaGetLastError());
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->sigma_transposed = !c->sigma_transposed;
+  c->lam32_built = c->lam_split_built = false;
+  oz_invalidate(c);
+  return DYSON_OK;
 }
 
 int dyson_observables(dyson_ctx* c, double* n, double* ekin, double* docc, int on_device) {
@@ -531,7 +737,8 @@ void dyson_destroy(dyson_ctx* c) {
   tc_release(c);
   oz_release(c);
   void* ptrs[] = {c->dU, c->dJ, c->d_nbr, c->d_nbond, c->d_eps, c->d_phase, c->d_lam, c->d_JW, c->d_Jz,
-                  c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_col_src, c->d_norm};
+                  c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_src_site, c->d_src_time,
+                  c->d_norm, c->adj};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_norm) cudaFreeHost(c->h_norm);

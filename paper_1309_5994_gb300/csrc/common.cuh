@@ -42,25 +42,32 @@ void launch_lam_c64(const double2* lam, int Nr, int Nt, int Nm, double dt, doubl
 void launch_lam_emb_split(const double2* lam, int Nr, int Nt, int Nm, double dt, double beta,
                           float* hi, float* lo, cudaStream_t s);
 
-// chunk state: FP64 state [Nr][ncol][Nc] complex128, FP32 state [Nr][ncol][2Nc] planar
-void launch_init_rhs(const double2* lam, const int* col_src, int Nr, int Nc, int ncol, double2* G,
-                     unsigned long long* scale, cudaStream_t s);
+// transpose every Nc x Nc block of lam in place
+void launch_transpose_blocks(double2* lam, int Nr, int Nc, cudaStream_t s);
+
+// Chunk state: FP64 [Nr][ncol][Nc] complex128, FP32 [Nr][ncol][2Nc] planar.  Vector
+// column n has the source (src_site[n], src_time[n]) (site -1: a zero padding column);
+// norms and scales are kept per group of gs consecutive columns (q = n / gs).
+void launch_init_rhs(const double2* lam, const int* src_site, const int* src_time, int Nr, int Nc, int ncol,
+                     int gs, double2* G, unsigned long long* scale, cudaStream_t s);
 // K3: out = B + K Gin (mode 0), or B + K Gin - Gin (mode 1); norm[q] = max |out - Gin| (mode 0)
 // or max |out| (mode 1).  If out32 != nullptr (mode 1 only) the result is written as FP32
 // planar state instead of into out.
 void launch_sweep_f64(const double2* lam, const double2* JW, const int* nbr, const int* nbond,
-                      const double2* Gin, double2* out, float* out32, const int* col_src, int Nr,
-                      int Nc, int ncol, int mode, unsigned long long* norm, cudaStream_t s);
+                      const double2* Gin, double2* out, float* out32, const int* src_site, const int* src_time,
+                      int Nr, int Nc, int ncol, int gs, int mode, unsigned long long* norm, cudaStream_t s);
 // SIMT FP32 sweep: dout = r + K din over planar FP32 state; norm[q] = max |dout - din|
 void launch_sweep_f32_simt(const float2* lam32, const float* Jz, const int* nbr, const int* nbond,
-                           const float* r, const float* din, float* dout, int Nr, int Nc, int ncol,
+                           const float* r, const float* din, float* dout, int Nr, int Nc, int ncol, int gs,
                            unsigned long long* norm, cudaStream_t s);
+// out[n][j][z] = G[j][n][z] for the first nv vector columns
+void launch_export_vectors(const double2* G, int Nr, int Nc, int ncol, int nv, double2* out, cudaStream_t s);
 // FP64 interleaved state -> FP32 planar state
 void launch_to_planar32(const double2* G, float* out, size_t n_el, int Nc, cudaStream_t s);
 // G64 += d32
 void launch_accumulate(double2* G, const float* d, int Nr, int Nc, int ncol, cudaStream_t s);
 // observables of the block columns of a chunk
-void launch_observables(const double2* G, const int* col_src, int nq, const int* nbr,
+void launch_observables(const double2* G, const int* src_site, int nq, const int* nbr,
                         const int* nbond, const double* Jtab, const double* eps, const double* U,
                         int Nr, int Nt, int Nc, int ncol, double dt, double* obs, cudaStream_t s);
 // [j][q*Nc+z'][z] -> user layout [q][j][z][z']
@@ -92,12 +99,15 @@ struct dyson_ctx {
   float* d_lam_lo = nullptr;
   double* d_obs = nullptr;           // [3][Nr][Nt]
   bool sigma_built = false;
+  bool sigma_transposed = false;     // every Lambda_i block transposed: solves give rows of G
 
   // work buffers, grown on demand
   void* work = nullptr;
   size_t work_bytes = 0;
-  int* d_col_src = nullptr;
-  int col_src_cap = 0;
+  int* d_src_site = nullptr;         // per vector column of the current chunk
+  int* d_src_time = nullptr;
+  int src_cap = 0;
+  std::vector<int> h_src_site, h_src_time;
   unsigned long long* d_norm = nullptr;   // [2 * max block columns]
   unsigned long long* h_norm = nullptr;   // pinned mirror
   int norm_cap = 0;
@@ -121,6 +131,8 @@ struct dyson_ctx {
   int64_t prof_launches[DYSON_KERNEL_KINDS] = {};
 
   void* tc = nullptr;                // tensor-core module state (tensor maps, workspace)
+  void* adj = nullptr;               // adjoint buffers (columns, rows, gathers, M, results)
+  size_t adj_bytes = 0;
   void* oz = nullptr;                // split-product residual state (slices, scales, maps)
   bool oz_enabled = true;            // DYSON_NO_OZ=1 keeps the FP64 CUDA-core residual
   bool use_oz = false;               // chosen for the current solve
@@ -129,6 +141,10 @@ struct dyson_ctx {
 };
 
 int ctx_fail(dyson_ctx* c, int code, const std::string& msg);
+
+// adjoint contractions (k_adjoint.cu): C, R columns of G and G^T at (i, zf) as [i][j][z]
+int adjoint_contract(dyson_ctx* c, const double2* C, const double2* R, const double* w_dev, int zf, double2* gam,
+                     double2* rho, double2* M, double* loss_dev, double* gU_dev, double* gJ_dev);
 #define DY_CUDA(ctx, call)                                                              \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \

@@ -202,8 +202,9 @@ __host__ __device__ constexpr Prod prod_of(int p) {
 __global__ void __launch_bounds__(THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap xmap,
               const double* __restrict__ sigma, const double* __restrict__ tau, const double2* __restrict__ G,
-              const double2* __restrict__ lam, const int* __restrict__ col_src, int Nc, int ncol,
-              float* __restrict__ r32, unsigned long long* __restrict__ norm, int* __restrict__ err) {
+              const double2* __restrict__ lam, const int* __restrict__ src_site, const int* __restrict__ src_time,
+              int Nc, int ncol, int gs, float* __restrict__ r32, unsigned long long* __restrict__ norm,
+              int* __restrict__ err) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -287,12 +288,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int m = mt * BM + q4 * 32 + lane;            // planar row: part m / Nc, contour row z = m % Nc
       const int z = m % Nc, part = m / Nc;
       const double sg = sigma[(size_t)site * N2 + m] * ldexp(1.0, -FIX);   // row scale / fixed-point unit
-      int qcur = (nt * BN) / Nc;
+      int qcur = (nt * BN) / gs;
       float runmax = 0.f;
       for (int c = 0; c < BN / 32; ++c) {
         const int n0 = nt * BN + c * 32;
-        if (n0 >= ncol) break;                          // warp-uniform; ncol is a multiple of 64
-        const int q = n0 / Nc;
+        if (n0 >= ncol) break;                          // warp-uniform; ncol and gs are multiples of 32
+        const int q = n0 / gs;
         if (q != qcur) {
           float mm = runmax;
 #pragma unroll
@@ -314,14 +315,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) acc[j] += f32_to_fixed(__uint_as_float(rr[j]));
         }
-        const bool src = (col_src[q] == site);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + j;
           const double2 g = G[((size_t)site * ncol + n) * Nc + z];
           double b = 0.0;
-          if (src) {
-            const double2 lv = lam[((size_t)site * Nc + z) * Nc + (n - q * Nc)];
+          if (src_site[n] == site) {                    // B = Lambda_s e_{z'} on the source site
+            const double2 lv = lam[((size_t)site * Nc + z) * Nc + src_time[n]];
             b = part ? lv.y : lv.x;
           }
           const double rv = b + (double)acc[j] * (sg * tau[(size_t)site * ncol + n]) - (part ? g.y : g.x);
@@ -404,9 +404,9 @@ void oz_invalidate(dyson_ctx* c) {
   if (c->oz) static_cast<OzState*>(c->oz)->a_ready = false;
 }
 
-int oz_residual(dyson_ctx* c, int nq, const double2* G, float* r32) {
+int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32) {
   OzState* st = state(c);
-  const int Nr = c->Nr, Nc = c->Nc, N2 = 2 * Nc, ncol = nq * Nc;
+  const int Nr = c->Nr, Nc = c->Nc, N2 = 2 * Nc;
   int rc;
   if (!st->d_err) {
     DY_CUDA(c, cudaMalloc(&st->d_err, sizeof(int)));
@@ -442,7 +442,8 @@ int oz_residual(dyson_ctx* c, int nq, const double2* G, float* r32) {
                                                                 ncol, st->xslices, st->tau);
   dim3 grid(N2 / BM, (ncol + BN - 1) / BN, Nr);
   k_oz_gemm<<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
-                                                      c->d_col_src, Nc, ncol, r32, c->d_norm, st->d_err);
+                                                      c->d_src_site, c->d_src_time, Nc, ncol, gs, r32, c->d_norm,
+                                                      st->d_err);
   c->launches += 2;
   DY_CUDA(c, cudaGetLastError());
   return DYSON_OK;

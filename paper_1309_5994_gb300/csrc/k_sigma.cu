@@ -135,6 +135,29 @@ __global__ void k_lam_emb_split(const double2* __restrict__ lam, int Nt, int Nm,
   }
 }
 
+// In-place transpose of each Nc x Nc block: the CTA of tile pair (bi, bj), bi <= bj,
+// swaps tile (bi, bj) with the transpose of tile (bj, bi) through shared memory.
+__global__ void k_transpose_blocks(double2* __restrict__ lam, int Nc) {
+  __shared__ double2 ta[32][33], tb[32][33];
+  const int tiles = (Nc + 31) / 32;
+  const int bi = blockIdx.x / tiles, bj = blockIdx.x % tiles;
+  if (bi > bj) return;
+  double2* L = lam + (size_t)blockIdx.y * Nc * Nc;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int zi = bi * 32 + r, zj = bj * 32 + threadIdx.x;
+    if (zi < Nc && zj < Nc) ta[r][threadIdx.x] = L[(size_t)zi * Nc + zj];
+    const int yi = bj * 32 + r, yj = bi * 32 + threadIdx.x;
+    if (yi < Nc && yj < Nc) tb[r][threadIdx.x] = L[(size_t)yi * Nc + yj];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int zi = bi * 32 + r, zj = bj * 32 + threadIdx.x;     // (bi, bj) <- transpose of (bj, bi)
+    if (zi < Nc && zj < Nc) L[(size_t)zi * Nc + zj] = tb[threadIdx.x][r];
+    const int yi = bj * 32 + r, yj = bi * 32 + threadIdx.x;     // (bj, bi) <- transpose of (bi, bj)
+    if (yi < Nc && yj < Nc) L[(size_t)yi * Nc + yj] = ta[threadIdx.x][r];
+  }
+}
+
 int grid_for(size_t total, int threads) {
   size_t b = (total + threads - 1) / threads;
   return (int)(b > 152 * 64 ? 152 * 64 : (b < 1 ? 1 : b));
@@ -170,4 +193,9 @@ void launch_lam_emb_split(const double2* lam, int Nr, int Nt, int Nm, double dt,
   int Nc = 2 * Nt + Nm;
   size_t total = (size_t)Nr * 4 * Nc * Nc;
   k_lam_emb_split<<<grid_for(total, 256), 256, 0, s>>>(lam, Nt, Nm, dt, beta, hi, lo, Nr);
+}
+
+void launch_transpose_blocks(double2* lam, int Nr, int Nc, cudaStream_t s) {
+  const int tiles = (Nc + 31) / 32;
+  k_transpose_blocks<<<dim3(tiles * tiles, Nr), dim3(32, 8), 0, s>>>(lam, Nc);
 }

@@ -13,8 +13,8 @@ namespace {
 
 constexpr int TZ = 64, TN = 64;
 
-// max over the 64 columns of a tile, one global atomic per block column touched
-__device__ void tile_norm_flush(unsigned long long* smax, int n0, int ncol, int Nc,
+// max over the 64 columns of a tile, one global atomic per column group (gs columns) touched
+__device__ void tile_norm_flush(unsigned long long* smax, int n0, int ncol, int gs,
                                 unsigned long long* __restrict__ norm) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -23,7 +23,7 @@ __device__ void tile_norm_flush(unsigned long long* smax, int n0, int ncol, int 
     for (int c = 0; c < TN; ++c) {
       int n = n0 + c;
       if (n >= ncol) break;
-      int q = n / Nc;
+      int q = n / gs;
       if (q != qcur) {
         if (qcur >= 0 && m) atomicMax(norm + qcur, m);
         qcur = q;
@@ -46,8 +46,8 @@ template <int MODE>
 __global__ __launch_bounds__(256) void k_sweep_f64(
     const double2* __restrict__ lam, const double2* __restrict__ JW, const int* __restrict__ nbr,
     const int* __restrict__ nbond, const double2* __restrict__ Gin, double2* __restrict__ out,
-    float* __restrict__ out32, const int* __restrict__ col_src, int Nc, int ncol,
-    unsigned long long* __restrict__ norm) {
+    float* __restrict__ out32, const int* __restrict__ src_site, const int* __restrict__ src_time, int Nc,
+    int ncol, int gs, unsigned long long* __restrict__ norm) {
   constexpr int KT = 16;
   __shared__ double2 As[TZ][KT + 1];
   __shared__ double2 Xs[TN][KT + 1];
@@ -120,8 +120,8 @@ __global__ __launch_bounds__(256) void k_sweep_f64(
     int n = n0 + tn + 16 * c;
     double m = 0.0;
     if (n < ncol) {
-      int q = n / Nc, zp = n - q * Nc;
-      bool src = (col_src[q] == i);
+      const int zp = src_time[n];
+      const bool src = (src_site[n] == i);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         int z = z0 + tz + 16 * r;
@@ -156,7 +156,7 @@ __global__ __launch_bounds__(256) void k_sweep_f64(
     }
     if (tz == 0) smax[tn + 16 * c] = mb;
   }
-  tile_norm_flush(smax, n0, ncol, Nc, norm);
+  tile_norm_flush(smax, n0, ncol, gs, norm);
 }
 
 // SIMT FP32 sweep over planar state: dout = r + Lambda' X, Lambda' = Lambda * W (complex64),
@@ -164,7 +164,7 @@ __global__ __launch_bounds__(256) void k_sweep_f64(
 __global__ __launch_bounds__(256) void k_sweep_f32_simt(
     const float2* __restrict__ lam32, const float* __restrict__ Jz, const int* __restrict__ nbr,
     const int* __restrict__ nbond, const float* __restrict__ r, const float* __restrict__ din,
-    float* __restrict__ dout, int Nc, int ncol, unsigned long long* __restrict__ norm) {
+    float* __restrict__ dout, int Nc, int ncol, int gs, unsigned long long* __restrict__ norm) {
   constexpr int KT = 32;
   __shared__ float2 As[TZ][KT + 1];
   __shared__ float2 Xs[TN][KT + 1];
@@ -256,37 +256,29 @@ __global__ __launch_bounds__(256) void k_sweep_f32_simt(
     }
     if (tz == 0) smax[tn + 16 * c] = mb;
   }
-  tile_norm_flush(smax, n0, ncol, Nc, norm);
+  tile_norm_flush(smax, n0, ncol, gs, norm);
 }
 
-// B = Lambda delta_s: G[s][q*Nc + z'][z] = Lambda_s[z][z'] (transposed through shared
-// memory); scale[q] = max |Lambda_s|.  G must be zeroed before.
-__global__ void k_init_rhs(const double2* __restrict__ lam, const int* __restrict__ col_src, int Nc, int ncol,
-                           double2* __restrict__ G, unsigned long long* __restrict__ scale) {
-  __shared__ double2 t[32][33];
-  __shared__ double wmax[8];
-  int q = blockIdx.z, s = col_src[q];
-  int zp0 = blockIdx.x * 32, z0 = blockIdx.y * 32;
+// B = Lambda delta_s e_{z'}: for vector column n with source (s, z'), G[s][n][z] =
+// Lambda_s[z][z'] (one warp per column; s < 0 marks a padding column that stays
+// zero); scale[n / gs] = max |B| over the group.  G must be zeroed before.
+__global__ void k_init_rhs(const double2* __restrict__ lam, const int* __restrict__ src_site,
+                           const int* __restrict__ src_time, int Nc, int ncol, int gs, double2* __restrict__ G,
+                           unsigned long long* __restrict__ scale) {
+  const int n = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (n >= ncol) return;
+  const int s = src_site[n], zp = src_time[n];
+  if (s < 0) return;
   const double2* L = lam + (size_t)s * Nc * Nc;
   double m = 0.0;
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    int z = z0 + r, zp = zp0 + threadIdx.x;
-    double2 v = (z < Nc && zp < Nc) ? L[(size_t)z * Nc + zp] : make_double2(0.0, 0.0);
-    t[r][threadIdx.x] = v;
+  for (int z = lane; z < Nc; z += 32) {
+    const double2 v = L[(size_t)z * Nc + zp];
+    G[((size_t)s * ncol + n) * Nc + z] = v;
     m = fmax(m, sqrt(v.x * v.x + v.y * v.y));
   }
-  __syncthreads();
-  for (int r = threadIdx.y; r < 32; r += 8) {
-    int zp = zp0 + r, z = z0 + threadIdx.x;
-    if (z < Nc && zp < Nc) G[((size_t)s * ncol + (size_t)q * Nc + zp) * Nc + z] = t[threadIdx.x][r];
-  }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (threadIdx.x == 0) wmax[threadIdx.y] = m;
-  __syncthreads();
-  if (threadIdx.x == 0 && threadIdx.y == 0) {
-    for (int w = 1; w < 8; ++w) m = fmax(m, wmax[w]);
-    atomicMax(scale + q, nonneg_bits(m));
-  }
+  if (lane == 0) atomicMax(scale + n / gs, nonneg_bits(m));
 }
 
 __global__ void k_accumulate(double2* __restrict__ G, const float* __restrict__ d, int Nc, size_t total) {
@@ -311,8 +303,9 @@ __global__ void k_to_planar32(const double2* __restrict__ G, float* __restrict__
   }
 }
 
-// K5: n, ekin, D of the source site of each block column (Sec. III.A, Eq. docc, App. B)
-__global__ void k_observables(const double2* __restrict__ G, const int* __restrict__ col_src,
+// K5: n, ekin, D of the source site of each block column (Sec. III.A, Eq. docc, App. B);
+// block column q holds vector columns q*Nc .. q*Nc + Nc - 1 of one source site
+__global__ void k_observables(const double2* __restrict__ G, const int* __restrict__ src_site,
                               const int* __restrict__ nbr, const int* __restrict__ nbond,
                               const double* __restrict__ Jtab, const double* __restrict__ eps,
                               const double* __restrict__ U, int Nr, int Nt, int Nc, int ncol, double dt,
@@ -320,7 +313,7 @@ __global__ void k_observables(const double2* __restrict__ G, const int* __restri
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   int q = blockIdx.y;
   if (k >= Nt) return;
-  int s = col_src[q];
+  int s = src_site[(size_t)q * Nc];
   size_t n = (size_t)q * Nc + k;  // source time t_k on the forward branch
   double2 geq = G[((size_t)s * ncol + n) * Nc + k];
   double dens = geq.y;            // Re(-i g) = Im g
@@ -363,6 +356,19 @@ __global__ void k_export(const double2* __restrict__ G, int Nr, int Nc, int nq, 
   }
 }
 
+// out[n][j][z] = G[j][n][z] for the first nv vector columns
+__global__ void k_export_vectors(const double2* __restrict__ G, int Nr, int Nc, int ncol, int nv,
+                                 double2* __restrict__ out) {
+  const size_t total = (size_t)nv * Nr * Nc;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int z = (int)(e % Nc);
+    const size_t rest = e / Nc;
+    const int j = (int)(rest % Nr);
+    const size_t n = rest / Nr;
+    out[e] = G[((size_t)j * ncol + n) * Nc + z];
+  }
+}
+
 int grid_for(size_t total, int threads) {
   size_t b = (total + threads - 1) / threads;
   return (int)(b > 152 * 64 ? 152 * 64 : (b < 1 ? 1 : b));
@@ -370,29 +376,34 @@ int grid_for(size_t total, int threads) {
 
 }  // namespace
 
-void launch_init_rhs(const double2* lam, const int* col_src, int Nr, int Nc, int ncol, double2* G,
-                     unsigned long long* scale, cudaStream_t s) {
+void launch_init_rhs(const double2* lam, const int* src_site, const int* src_time, int Nr, int Nc, int ncol, int gs,
+                     double2* G, unsigned long long* scale, cudaStream_t s) {
   (void)Nr;
-  int nq = ncol / Nc;
-  dim3 grd((Nc + 31) / 32, (Nc + 31) / 32, nq), blk(32, 8);
-  k_init_rhs<<<grd, blk, 0, s>>>(lam, col_src, Nc, ncol, G, scale);
+  k_init_rhs<<<(ncol + 7) / 8, 256, 0, s>>>(lam, src_site, src_time, Nc, ncol, gs, G, scale);
 }
 
 void launch_sweep_f64(const double2* lam, const double2* JW, const int* nbr, const int* nbond,
-                      const double2* Gin, double2* out, float* out32, const int* col_src, int Nr, int Nc,
-                      int ncol, int mode, unsigned long long* norm, cudaStream_t s) {
+                      const double2* Gin, double2* out, float* out32, const int* src_site, const int* src_time,
+                      int Nr, int Nc, int ncol, int gs, int mode, unsigned long long* norm, cudaStream_t s) {
   dim3 grd((ncol + TN - 1) / TN, (Nc + TZ - 1) / TZ, Nr);
   if (mode == 0)
-    k_sweep_f64<0><<<grd, 256, 0, s>>>(lam, JW, nbr, nbond, Gin, out, nullptr, col_src, Nc, ncol, norm);
+    k_sweep_f64<0><<<grd, 256, 0, s>>>(lam, JW, nbr, nbond, Gin, out, nullptr, src_site, src_time, Nc, ncol, gs,
+                                       norm);
   else
-    k_sweep_f64<1><<<grd, 256, 0, s>>>(lam, JW, nbr, nbond, Gin, out, out32, col_src, Nc, ncol, norm);
+    k_sweep_f64<1><<<grd, 256, 0, s>>>(lam, JW, nbr, nbond, Gin, out, out32, src_site, src_time, Nc, ncol, gs,
+                                       norm);
 }
 
 void launch_sweep_f32_simt(const float2* lam32, const float* Jz, const int* nbr, const int* nbond,
-                           const float* r, const float* din, float* dout, int Nr, int Nc, int ncol,
+                           const float* r, const float* din, float* dout, int Nr, int Nc, int ncol, int gs,
                            unsigned long long* norm, cudaStream_t s) {
   dim3 grd((ncol + TN - 1) / TN, (Nc + TZ - 1) / TZ, Nr);
-  k_sweep_f32_simt<<<grd, 256, 0, s>>>(lam32, Jz, nbr, nbond, r, din, dout, Nc, ncol, norm);
+  k_sweep_f32_simt<<<grd, 256, 0, s>>>(lam32, Jz, nbr, nbond, r, din, dout, Nc, ncol, gs, norm);
+}
+
+void launch_export_vectors(const double2* G, int Nr, int Nc, int ncol, int nv, double2* out, cudaStream_t s) {
+  const size_t total = (size_t)nv * Nr * Nc;
+  k_export_vectors<<<grid_for(total, 256), 256, 0, s>>>(G, Nr, Nc, ncol, nv, out);
 }
 
 void launch_accumulate(double2* G, const float* d, int Nr, int Nc, int ncol, cudaStream_t s) {
@@ -404,10 +415,10 @@ void launch_to_planar32(const double2* G, float* out, size_t n_el, int Nc, cudaS
   k_to_planar32<<<grid_for(n_el, 256), 256, 0, s>>>(G, out, Nc, n_el);
 }
 
-void launch_observables(const double2* G, const int* col_src, int nq, const int* nbr, const int* nbond,
+void launch_observables(const double2* G, const int* src_site, int nq, const int* nbr, const int* nbond,
                         const double* Jtab, const double* eps, const double* U, int Nr, int Nt, int Nc,
                         int ncol, double dt, double* obs, cudaStream_t s) {
-  k_observables<<<dim3((Nt + 127) / 128, nq), 128, 0, s>>>(G, col_src, nbr, nbond, Jtab, eps, U, Nr, Nt, Nc,
+  k_observables<<<dim3((Nt + 127) / 128, nq), 128, 0, s>>>(G, src_site, nbr, nbond, Jtab, eps, U, Nr, Nt, Nc,
                                                           ncol, dt, obs);
 }
 

@@ -116,7 +116,7 @@ __global__ __launch_bounds__(256) void k_tc_gather(const float* __restrict__ din
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
               const __grid_constant__ CUtensorMap map_x, const float* __restrict__ r, const float* __restrict__ din,
-              float* __restrict__ dout, int Nr, int Nc, int ncol, unsigned long long* __restrict__ norm,
+              float* __restrict__ dout, int Nr, int Nc, int ncol, int gs, unsigned long long* __restrict__ norm,
               int* __restrict__ err) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
@@ -259,13 +259,13 @@ __global__ void __launch_bounds__(THREADS, 1)
       tc_fence_after();
       const int mg = mt * BM + q4 * 32 + lane;          // row of the 2Nc planar vector
       const int n_first = nt * BN;
-      int qcur = n_first / Nc;
+      int qcur = n_first / gs;
       float runmax = 0.f;
-      // Nc is a multiple of 64, so a chunk of 32 columns lies in one block column
+      // gs is a multiple of 32, so a chunk of 32 columns lies in one norm group
       for (int c = 0; c < BN / 32; ++c) {
         const int n0 = n_first + c * 32;
         if (n0 >= ncol) break;                          // uniform across the warp
-        const int q = n0 / Nc;
+        const int q = n0 / gs;
         if (q != qcur) {
           float m = runmax;
 #pragma unroll
@@ -353,10 +353,9 @@ bool tc_supported(dyson_ctx* c, int Nc) {
   return Nc % 64 == 0 && encode_fn() != nullptr;
 }
 
-int tc_sweep(dyson_ctx* c, int nq, const float* r, const float* din, float* dout) {
+int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout) {
   TcState* st = state(c);
   const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;
-  const int ncol = nq * Nc;
   if (!st->d_err) {
     DY_CUDA(c, cudaMalloc(&st->d_err, sizeof(int)));
     DY_CUDA(c, cudaMemsetAsync(st->d_err, 0, sizeof(int), c->stream));
@@ -397,7 +396,7 @@ int tc_sweep(dyson_ctx* c, int nq, const float* r, const float* din, float* dout
   k_tc_gather<<<gblocks, 256, 0, c->stream>>>(din, c->d_Jz, c->d_nbr, c->d_nbond, st->xbuf, Nr, Nc, ncol);
   const long long tiles = (long long)(N2 / BM) * ((ncol + BN - 1) / BN) * Nr;
   const int grid = (int)std::min<long long>(tiles, st->num_sms > 0 ? st->num_sms : 148);
-  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->a_hi, st->a_lo, st->x, r, din, dout, Nr, Nc, ncol,
+  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->a_hi, st->a_lo, st->x, r, din, dout, Nr, Nc, ncol, gs,
                                                        c->d_norm, st->d_err);
   DY_CUDA(c, cudaGetLastError());
   c->launches += 2;

@@ -4,8 +4,9 @@
 
 // true when the 3xTF32 tcgen05 sweep supports this contour length
 bool tc_supported(dyson_ctx* c, int Nc);
-// one sweep d_out = r + K d_in over the FP32 planar chunk state; writes c->d_norm[q]
-int tc_sweep(dyson_ctx* c, int nq, const float* r, const float* d_in, float* d_out);
+// one sweep d_out = r + K d_in over the FP32 planar chunk state of ncol vector columns;
+// writes c->d_norm[q] for groups of gs columns (gs a multiple of 32, Nc a multiple of 64)
+int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* d_in, float* d_out);
 // DYSON_ERR_TIMEOUT if a bounded pipeline wait of an earlier sweep expired (clears the flag)
 int tc_check_error(dyson_ctx* c);
 // free tensor-core module state
