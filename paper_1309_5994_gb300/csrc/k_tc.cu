@@ -32,6 +32,7 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 32, STAGES = 2;
+constexpr int PREFETCH = 4;                            // k-blocks of L2 prefetch ahead of the loads
 constexpr int A_TILE = BM * BK * 4;                    // 16 KB
 constexpr int X_TILE = BN * BK * 4;                    // 32 KB
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * X_TILE;   // A_hi, A_lo, X (-> X_hi), X_lo
@@ -59,10 +60,12 @@ struct TcState {
   int num_sms = 0;
 };
 
+// Round to TF32 (10 explicit mantissa bits), to nearest with ties away from zero,
+// by integer arithmetic on the bit pattern: adding half of the 13 dropped bits
+// then clearing them rounds the magnitude (sign-magnitude encoding).  Two
+// full-rate integer instructions instead of a conversion instruction.
 __device__ __forceinline__ float to_tf32(float v) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ unsigned long long nonneg_bits(float v) {
@@ -171,6 +174,19 @@ __global__ void __launch_bounds__(THREADS, 1)
           tma_load_3d(st, &map_ahi, &full_tma[s], kb * BK, mt * BM, site);
           tma_load_3d(st + A_TILE, &map_alo, &full_tma[s], kb * BK, mt * BM, site);
           tma_load_3d(st + 2 * A_TILE, &map_x, &full_tma[s], kb * BK, nt * BN, site);
+          // warm L2 with the tiles of the k-block PREFETCH steps ahead: the stage
+          // loads then see L2 latency instead of DRAM latency
+          {
+            const int ahead = kb + PREFETCH;
+            const int t2 = ahead < KB ? tile : tile + (int)gridDim.x;
+            if (t2 < tiles && (ahead < KB || ahead - KB < KB)) {
+              const int k2 = ahead < KB ? ahead : ahead - KB;
+              const int m2 = t2 % MT, n2 = (t2 / MT) % NT, s2 = t2 / (MT * NT);
+              tma_prefetch_3d(&map_ahi, k2 * BK, m2 * BM, s2);
+              tma_prefetch_3d(&map_alo, k2 * BK, m2 * BM, s2);
+              tma_prefetch_3d(&map_x, k2 * BK, n2 * BN, s2);
+            }
+          }
         }
       }
       // let every copy this thread issued land before the CTA can exit

@@ -76,6 +76,26 @@ def test_adjoint_matches_oracle(torch_cuda, lib, kw):
         assert np.abs(gJg - gJ).max() < 1e-10 * max(1.0, np.abs(gJ).max())
 
 
+def test_autograd_amplitude_gradient(torch_cuda, lib):
+    """The drive built from a torch scalar s: s.grad through torch.autograd equals
+    the oracle's chain rule of its adjoint gradients."""
+    torch = torch_cuda
+    from paper_1309_5994_gb300.autograd import weighted_density
+    kw = dict(L=2, Ly=3, Nt=24, Nm=16, dt=0.05, trap_c=0.3, U0=20.0, aU=0.1, aJ=0.2, omega=20.0)
+    p = wl.small(**kw)
+    w = np.random.default_rng(8).uniform(0, 1, p.Nr)
+    s = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    t = torch.arange(p.Nt, dtype=torch.float64) * p.dt
+    U = (20.0 * (1 + 0.1 * s * torch.sin(20 * t))).expand(p.Nr, p.Nt)
+    J = (1.0 - 0.2 * s * torch.sin(20 * t)).expand(p.Nb, p.Nt)
+    L = weighted_density(U, J, p, w, precision=1, tol=1e-13)
+    L.backward()
+    Lo, gU, gJ = adjoint.gradients(wl.small(**kw, amp=1.0), w)
+    dU, dJ = wl.drive_derivative_tables(wl.small(**kw, amp=1.0))
+    assert abs(L.item() - Lo) < 1e-12
+    assert abs(s.grad.item() - float(np.sum(gU * dU) + np.sum(gJ * dJ))) < 1e-10 * max(1.0, abs(s.grad.item()))
+
+
 def test_config5_amplitude_gradient_matches_finite_differences(torch_cuda, lib):
     """24x24 lattice, Nc = 256, config-3 drive scaled by s: d/ds of
     sum_i w_i n_i(t_final) from the adjoint (chain rule through the U and J
