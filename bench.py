@@ -50,7 +50,32 @@ def parse():
     ap.add_argument("--f64-columns", type=int, default=2, help="block columns timed on the plain FP64 path")
     ap.add_argument("--cpu-columns", type=int, default=32, help="vector columns in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU legs (profiling runs)")
+    ap.add_argument("--lattice", type=int, default=16,
+                    help="lattice side; 16 is the benchmark workload, smaller sides serve ncu captures only")
     return ap.parse_args()
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_config2_16cols.json")
+
+
+def load_traffic():
+    """DRAM bytes per launch of each kernel kind at the benchmark size, from an ncu
+    capture (profiles/), kept only while the kernel's source is unchanged."""
+    import hashlib
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except OSError:
+        return {}
+    out = {}
+    for name, e in rec.get("kernels", {}).items():
+        try:
+            with open(os.path.join(ROOT, e["source"]), "rb") as f:
+                same = hashlib.sha256(f.read()).hexdigest() == e["sha256"]
+        except OSError:
+            same = False
+        out[name] = e["bytes_per_launch"] if same else None
+    return out
 
 
 def load_peaks():
@@ -187,7 +212,8 @@ def run_gb300(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p = wl.config2()
+    p = wl.config2() if args.lattice == 16 else wl.uniform_problem(
+        f"c2_L{args.lattice}_Nc256", args.lattice, 112, 32, 0.05, 2.0, 0.0, 0.02, 20.0, 1.0)
     stream = torch.cuda.Stream(device=dev)
     solver = binding.Solver(p, device=local, stream=stream)
     PREC = binding.PREC_TF32X3_F64REF
@@ -231,29 +257,49 @@ def run_gb300(args, rank, world, local):
     refinements = [r["refinements"] for r in reports]
     residual = max(r["residual"] for r in reports)
 
-    # ---- roofline of the kernel with the largest device time ----
+    # ---- rooflines per kernel kind; the one with the largest device time is reported ----
     peaks, peak_src = load_peaks()
+    traffic = load_traffic() if args.lattice == 16 else {}
     Nc, Nr = p.Nc, p.Nr
-    alg_flops_per_launch = 8.0 * Nc ** 3 * Nr * args.batch
-    dom_name, (dom_n, dom_ms) = max(kstats.items(), key=lambda kv: kv[1][1])
-    achieved = alg_flops_per_launch / (dom_ms / dom_n * 1e-3) / 1e12 if dom_n else 0.0
-    if dom_name == "residual_f64" or dom_name == "sweep_f64":
-        roof = {"bound": "alu", "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64 rate from SM count x FP64 flop/clk x max clock (no measured FP64 peak)"}
-    elif dom_name == "residual_split_bf16":
-        peak = peaks["bf16_tflops"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "executed_tflops": 28 * achieved,
-                "peak_source": f"{peak_src} bf16 burst; achieved counts algorithmic complex-GEMM flops "
-                               f"(8 Nc^3 per site and block column), the 7-slice split executes 28 BF16 products"}
-    else:
-        peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "executed_tflops": 3 * achieved,
-                "peak_source": f"{peak_src} bf16 burst x nominal tf32/bf16 ratio; achieved counts algorithmic "
-                               f"complex-GEMM flops (8 Nc^3 per site and block column), the 3xTF32 split executes 3x"}
-    roof["kernel"] = dom_name
+    ncol = args.batch * Nc
+    alg_flops = 8.0 * Nc * Nc * Nr * ncol                   # contour-GEMM flops of one sweep / residual
+    state_bytes = 2.0 * Nc * 4 * Nr * ncol                  # one FP32 planar chunk state
+    note = "achieved counts algorithmic complex-GEMM flops (8 Nc^2 per site and vector column)"
+    rooflines = {}
+    for name, (n, ms) in kstats.items():
+        if not n:
+            continue
+        dur = ms / n * 1e-3
+        if name == "gather_tc":
+            ach = 2 * state_bytes / dur / 1e9
+            peak = peaks["hbm_gbs"]
+            r = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                 "algorithmic_bytes_per_launch": 2 * state_bytes,
+                 "peak_source": f"{peak_src} copy bandwidth; bytes = read d + write X (FP32 planar state)"}
+        elif name in ("sweep_f64", "residual_f64"):
+            ach = alg_flops / dur / 1e12
+            r = {"bound": "alu", "achieved": ach, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                 "frac": ach / NOMINAL_FP64_TFLOPS,
+                 "peak_source": "nominal FP64 rate from SM count x FP64 flop/clk x max clock (no measured FP64 peak)"}
+        elif name == "residual_split_bf16":
+            ach = alg_flops / dur / 1e12
+            peak = peaks["bf16_tflops"]
+            r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                 "executed_tflops": 28 * ach,
+                 "peak_source": f"{peak_src} bf16 burst; {note}, the 7-slice split executes 28 BF16 products"}
+        else:
+            ach = alg_flops / dur / 1e12
+            peak = peaks["bf16_tflops"] * NOMINAL_TF32_OVER_BF16
+            r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                 "executed_tflops": 3 * ach, "executed_frac": 3 * ach / peak,
+                 "peak_source": f"{peak_src} bf16 burst x nominal tf32/bf16 ratio; {note}, the 3xTF32 split "
+                                f"executes 3x"}
+        r["traffic"] = traffic.get(name)
+        r["kernel"] = name
+        r["avg_ms"] = ms / n
+        rooflines[name] = r
+    dom_name = max(kstats.items(), key=lambda kv: kv[1][1])[0]
+    roof = rooflines[dom_name]
     kernels = {nm: {"launches": n, "avg_ms": (ms / n if n else None), "total_ms": ms,
                     "share": ms / max(sum(v[1] for v in kstats.values()), 1e-9)}
                for nm, (n, ms) in kstats.items() if n}
@@ -317,7 +363,9 @@ def run_gb300(args, rank, world, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "tf32x3+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "block_columns_per_step_per_gpu": args.batch,
+            "config": {"workload": WORKLOAD if args.lattice == 16 else
+                       f"profiling case, not the benchmark: {args.lattice}x{args.lattice} lattice on the same contour",
+                       "block_columns_per_step_per_gpu": args.batch,
                        "precision": "3xTF32 tcgen05 series sweeps + FP64 Dyson residual refinement",
                        "tol_rel_residual": args.tol, "lattice": [p.Lx, p.Ly], "Nc": Nc,
                        "l2": f"inputs larger than L2: {48 * Nr * Nc * Nc * args.batch / 1e9:.1f} GB of state per step",
@@ -325,7 +373,8 @@ def run_gb300(args, rank, world, local):
             "contour_gemm_tflops": tflops_local * world,
             "vector_columns_per_s": value * Nc,
             "sweeps_per_step": sweeps, "refinements_per_step": refinements, "max_rel_residual": residual,
-            "roofline": roof, "kernels": kernels, "clocks": clk, "gpu_launches": gpu_launches}
+            "roofline": roof, "rooflines": rooflines, "kernels": kernels, "clocks": clk,
+            "gpu_launches": gpu_launches}
     line.update(extras)
     print(json.dumps(line), flush=True)
 

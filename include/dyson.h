@@ -182,10 +182,12 @@ const char* dyson_last_error(const dyson_ctx* ctx);
 enum {
   DYSON_KERNEL_SWEEP_F64 = 0,     /* FP64 series sweep (gather + complex GEMM)               */
   DYSON_KERNEL_SWEEP_F32 = 1,     /* FP32 CUDA-core sweep                                    */
-  DYSON_KERNEL_SWEEP_TC = 2,      /* 3xTF32 tcgen05 sweep (gather + split + GEMM)            */
+  DYSON_KERNEL_SWEEP_TC = 2,      /* 3xTF32 tcgen05 sweep GEMM (split + MMA + epilogue)      */
   DYSON_KERNEL_RESIDUAL_F64 = 3,  /* FP64 Dyson residual r = Lambda delta + K G - G          */
   DYSON_KERNEL_RESIDUAL_SPLIT = 4,/* the same residual from BF16 slice products on tcgen05   */
-  DYSON_KERNEL_KINDS = 5
+  DYSON_KERNEL_SWEEP_TC_PAIR = 5, /* the same GEMM on CTA pairs (tcgen05 cta_group::2, M=256) */
+  DYSON_KERNEL_GATHER_TC = 6,     /* neighbour gather X = J d of the tensor-core sweep        */
+  DYSON_KERNEL_KINDS = 7
 };
 
 /* Enable (1) or disable (0) event timing of every sweep/residual launch on the
@@ -201,6 +203,16 @@ int64_t dyson_launch_count(const dyson_ctx* ctx);
 
 /* Cap the number of block columns solved together (0 = size from free memory). */
 int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);
+
+/* Form of the 3xTF32 tensor-core sweep.  SINGLE_CTA: one CTA per 128 x 256
+ * output tile (the default).  CTA_PAIR: clusters of two CTAs on 256 x 256 tiles
+ * with tcgen05 cta_group::2 MMAs; used only when Nc is a multiple of 128 and
+ * the device can co-schedule CTA pairs, otherwise the single-CTA form runs.
+ * Both give the same results to FP32 rounding; which is faster depends on the
+ * shape, which is what dyson_autotune measures.  Returns INVALID_ARG for an
+ * unknown variant. */
+enum { DYSON_SWEEP_SINGLE_CTA = 0, DYSON_SWEEP_CTA_PAIR = 1 };
+int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free solve of one block column.  The paper has no counterpart:

@@ -21,8 +21,9 @@ ERR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_CONVERGED", -4: "DI
 PREC_F64 = 0
 PREC_TF32X3_F64REF = 1
 KERNEL_SWEEP_F64, KERNEL_SWEEP_F32, KERNEL_SWEEP_TC, KERNEL_RESIDUAL_F64, KERNEL_RESIDUAL_SPLIT = 0, 1, 2, 3, 4
+KERNEL_SWEEP_TC_PAIR, KERNEL_GATHER_TC = 5, 6
 KERNEL_NAMES = {0: "sweep_f64", 1: "sweep_f32_simt", 2: "sweep_tc_3xtf32", 3: "residual_f64",
-                4: "residual_split_bf16"}
+                4: "residual_split_bf16", 5: "sweep_tc_3xtf32_pair", 6: "gather_tc"}
 
 
 class Lattice(C.Structure):
@@ -54,7 +55,8 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_observables", "dyson_solve_vector_columns", "dyson_transpose_sigma", "dyson_adjoint",
            "dyson_profile", "dyson_profile_query", "dyson_set_chunk",
            "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
-           "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error"]
+           "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant"]
+SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
 
 
 def load(path: str = _LIB_PATH):
@@ -80,6 +82,7 @@ def load(path: str = _LIB_PATH):
     lib.dyson_profile.argtypes = [P, C.c_int]
     lib.dyson_profile_query.argtypes = [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     lib.dyson_set_chunk.argtypes = [P, C.c_int32]
+    lib.dyson_set_sweep_variant.argtypes = [P, C.c_int]
     lib.dyson_launch_count.argtypes = [P]
     lib.dyson_launch_count.restype = C.c_int64
     lib.dyson_solve_block_column_noalloc.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
@@ -215,6 +218,9 @@ class Solver:
 
     def set_chunk(self, cols: int):
         self._check(self.lib.dyson_set_chunk(self.h, cols))
+
+    def set_sweep_variant(self, variant: int):
+        self._check(self.lib.dyson_set_sweep_variant(self.h, variant))
 
     def profile(self, enable: bool):
         self._check(self.lib.dyson_profile(self.h, 1 if enable else 0))

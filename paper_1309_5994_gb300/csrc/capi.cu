@@ -201,8 +201,12 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
     if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
-      KernelTimer t(c, DYSON_KERNEL_SWEEP_TC);
-      if ((rc = tc_sweep(c, ncol, gs, r32, da, db))) return rc;
+      {
+        KernelTimer t(c, DYSON_KERNEL_GATHER_TC);
+        if ((rc = tc_sweep(c, ncol, gs, r32, da, db, TC_GATHER))) return rc;
+      }
+      KernelTimer t(c, tc_uses_pair(c) ? DYSON_KERNEL_SWEEP_TC_PAIR : DYSON_KERNEL_SWEEP_TC);
+      if ((rc = tc_sweep(c, ncol, gs, r32, da, db, TC_GEMM))) return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
       launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, ncol, gs,
@@ -353,6 +357,7 @@ int dyson_init(dyson_ctx** out, const dyson_lattice* L, const dyson_contour* C, 
   if (const char* e = std::getenv("DYSON_MAX_REFINEMENTS")) c->max_refinements = std::max(1, atoi(e));
   if (const char* e = std::getenv("DYSON_NO_TC")) c->tc_enabled = !(e[0] == '1');
   if (const char* e = std::getenv("DYSON_NO_OZ")) c->oz_enabled = !(e[0] == '1');
+  if (const char* e = std::getenv("DYSON_TC_PAIR")) c->tc_variant = (e[0] == '1') ? DYSON_SWEEP_CTA_PAIR : 0;
 
   // neighbour slots (+x, -x, +y, -y) with their bond indices
   std::vector<int> nbr((size_t)c->Nr * 4, -1), nbond((size_t)c->Nr * 4, -1);
@@ -726,6 +731,14 @@ int64_t dyson_launch_count(const dyson_ctx* c) { return c ? c->launches : -1; }
 int dyson_set_chunk(dyson_ctx* c, int32_t block_columns) {
   if (!c || block_columns < 0) return fail_noctx(DYSON_ERR_INVALID_ARG, "bad chunk size");
   c->chunk_override = block_columns;
+  return DYSON_OK;
+}
+
+int dyson_set_sweep_variant(dyson_ctx* c, int variant) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (variant != DYSON_SWEEP_SINGLE_CTA && variant != DYSON_SWEEP_CTA_PAIR)
+    return ctx_fail(c, DYSON_ERR_INVALID_ARG, "unknown sweep variant");
+  c->tc_variant = variant;
   return DYSON_OK;
 }
 

@@ -19,12 +19,16 @@
 //                               256-column TMEM accumulators
 //                  warps 8-11   epilogue: tcgen05.ld, + r, store d_out, update norm
 //                so the epilogue of one tile overlaps the MMAs of the next.
+//   k_tc_gemm_pair  the same sweep on clusters of two CTAs (tcgen05 cta_group::2,
+//                256 x 256 tiles, three 64 KB stages); selected per context with
+//                dyson_set_sweep_variant.
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the CTA
 // raises an error flag, lets in-flight copies and MMAs land, frees TMEM and
 // exits, and the host returns DYSON_ERR_TIMEOUT.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "ptx.cuh"
 #include "tc.cuh"
@@ -58,6 +62,11 @@ struct TcState {
   int* d_err = nullptr;
   bool smem_set = false;
   int num_sms = 0;
+  // CTA-pair kernel: X map with half-width boxes, co-resident clusters (0 = unused)
+  CUtensorMap xh;
+  int xh_ncol = -1;
+  const float* xh_ptr = nullptr;
+  int pair_clusters = -1;
 };
 
 // Round to TF32 (10 explicit mantissa bits), to nearest with ties away from zero,
@@ -111,6 +120,70 @@ __global__ __launch_bounds__(256) void k_tc_gather(const float* __restrict__ din
     }
     *reinterpret_cast<float4*>(X + ((size_t)i * ncol + n) * N2 + k) = acc;
   }
+}
+
+// split an fp32 tile (float4 granules e = tt, tt + 128, ...) into TF32 hi in place and lo at x + bytes
+template <int BYTES>
+__device__ __forceinline__ void split_tile(uint8_t* x, int tt) {
+  float4* xh = reinterpret_cast<float4*>(x);
+  float4* xl = reinterpret_cast<float4*>(x + BYTES);
+#pragma unroll 4
+  for (int e = tt; e < BYTES / 16; e += 128) {
+    float4 v = xh[e], h, l;
+    h.x = to_tf32(v.x); l.x = to_tf32(v.x - h.x);
+    h.y = to_tf32(v.y); l.y = to_tf32(v.y - h.y);
+    h.z = to_tf32(v.z); l.z = to_tf32(v.z - h.z);
+    h.w = to_tf32(v.w); l.w = to_tf32(v.w - h.w);
+    xh[e] = h;
+    xl[e] = l;
+  }
+}
+
+// epilogue of one warp's 32 accumulator lanes x BN columns (TMEM address tacc):
+// y = r + acc at planar row mg, columns n_first.., store y, and fold max|y - d_in|
+// into norm[] per group of gs columns (gs a multiple of 32)
+__device__ __forceinline__ void epilogue_rows(uint32_t tacc, int mg, int n_first, int site, int ncol, int gs,
+                                              size_t N2, const float* __restrict__ r, const float* __restrict__ din,
+                                              float* __restrict__ dout, unsigned long long* __restrict__ norm,
+                                              int lane) {
+  using namespace ptx;
+  int qcur = n_first / gs;
+  float runmax = 0.f;
+  for (int c = 0; c < BN / 32; ++c) {
+    const int n0 = n_first + c * 32;
+    if (n0 >= ncol) break;                          // uniform across the warp
+    const int q = n0 / gs;
+    if (q != qcur) {
+      float m = runmax;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) atomicMax(norm + qcur, nonneg_bits(m));
+      qcur = q;
+      runmax = 0.f;
+    }
+    float rv[32], dv[32];
+    uint32_t v[32];
+    const size_t base = ((size_t)site * ncol + n0) * N2 + mg;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      rv[j] = __ldcs(r + base + (size_t)j * N2);
+      dv[j] = __ldcs(din + base + (size_t)j * N2);
+    }
+    tmem_ld32(tacc + (uint32_t)(c * 32), v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float y = rv[j] + __uint_as_float(v[j]);
+      float d = fabsf(y - dv[j]);
+      d = (d == d) ? d : __int_as_float(0x7f800000);
+      __stcs(dout + base + (size_t)j * N2, y);
+      runmax = fmaxf(runmax, d);
+    }
+  }
+  float m = runmax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) atomicMax(norm + qcur, nonneg_bits(m));
 }
 
 // ---------------------------------------------------------------------------
@@ -245,18 +318,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           ok = false;
           break;
         }
-        float4* xh = reinterpret_cast<float4*>(stage_ptr(s) + 2 * A_TILE);
-        float4* xl = reinterpret_cast<float4*>(stage_ptr(s) + 2 * A_TILE + X_TILE);
-#pragma unroll 4
-        for (int e = tt; e < X_TILE / 16; e += 128) {
-          float4 v = xh[e], h, l;
-          h.x = to_tf32(v.x); l.x = to_tf32(v.x - h.x);
-          h.y = to_tf32(v.y); l.y = to_tf32(v.y - h.y);
-          h.z = to_tf32(v.z); l.z = to_tf32(v.z - h.z);
-          h.w = to_tf32(v.w); l.w = to_tf32(v.w - h.w);
-          xh[e] = h;
-          xl[e] = l;
-        }
+        split_tile<X_TILE>(stage_ptr(s) + 2 * A_TILE, tt);
         fence_async_smem();
         mbar_arrive(&full_split[s]);
       }
@@ -273,46 +335,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       go = __all_sync(0xffffffffu, go);                 // tcgen05.ld below is warp-collective
       if (!go) break;
       tc_fence_after();
-      const int mg = mt * BM + q4 * 32 + lane;          // row of the 2Nc planar vector
-      const int n_first = nt * BN;
-      int qcur = n_first / gs;
-      float runmax = 0.f;
-      // gs is a multiple of 32, so a chunk of 32 columns lies in one norm group
-      for (int c = 0; c < BN / 32; ++c) {
-        const int n0 = n_first + c * 32;
-        if (n0 >= ncol) break;                          // uniform across the warp
-        const int q = n0 / gs;
-        if (q != qcur) {
-          float m = runmax;
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-          if (lane == 0) atomicMax(norm + qcur, nonneg_bits(m));
-          qcur = q;
-          runmax = 0.f;
-        }
-        float rv[32], dv[32];
-        uint32_t v[32];
-        const size_t base = ((size_t)site * ncol + n0) * N2 + mg;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          rv[j] = __ldcs(r + base + (size_t)j * N2);
-          dv[j] = __ldcs(din + base + (size_t)j * N2);
-        }
-        tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS + c * 32), v);
-        tmem_wait_ld();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float y = rv[j] + __uint_as_float(v[j]);
-          float d = fabsf(y - dv[j]);
-          d = (d == d) ? d : __int_as_float(0x7f800000);
-          __stcs(dout + base + (size_t)j * N2, y);
-          runmax = fmaxf(runmax, d);
-        }
-      }
-      float m = runmax;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) atomicMax(norm + qcur, nonneg_bits(m));
+      epilogue_rows(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS), mt * BM + q4 * 32 + lane,
+                    nt * BN, site, ncol, gs, N2, r, din, dout, norm, lane);
       // this accumulator may be overwritten by the MMAs of tile t + 2
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
@@ -325,6 +349,202 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
+  }
+  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// CTA-pair form (cluster of 2, tcgen05 cta_group::2): the pair computes a
+// 256 x 256 tile with M = 256 MMAs.  CTA r of the pair loads Lambda rows
+// 128 r .. 128 r + 127 of the tile and X columns 128 r .. 128 r + 127, splits only
+// its half of X, and holds rows 128 r .. of the accumulator in its own TMEM.
+// The even CTA's MMA thread reads both CTAs' shared memory, so per SM the TMA,
+// split and MMA operand traffic through shared memory drop by a third, and
+// three 64 KB stages fit.  Pipeline:
+//   TMA (each CTA, own barrier) -> split (each CTA) -> arrive on the even CTA's
+//   full_split -> MMAs -> commit multicast to both CTAs' empty / acc_full ->
+//   epilogue (each CTA) -> arrive on the even CTA's acc_empty.
+// ---------------------------------------------------------------------------
+constexpr int PM = 256;                                 // tile rows per pair
+constexpr int PX_TILE = (BN / 2) * BK * 4;              // 16 KB: one CTA's half of the X tile
+constexpr int P_STAGES = 3;
+constexpr int P_STAGE_BYTES = 2 * A_TILE + 2 * PX_TILE;  // A_hi, A_lo, X (-> X_hi), X_lo
+constexpr int P_TMA_BYTES = 2 * A_TILE + PX_TILE;
+constexpr int P_SMEM_BYTES = P_STAGES * P_STAGE_BYTES + 1024;
+constexpr uint32_t P_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                             ((uint32_t)(PM >> 4) << 24);
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_gemm_pair(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
+                   const __grid_constant__ CUtensorMap map_xh, const float* __restrict__ r,
+                   const float* __restrict__ din, float* __restrict__ dout, int Nr, int Nc, int ncol, int gs,
+                   unsigned long long* __restrict__ norm, int* __restrict__ err) {
+  using namespace ptx;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_tma[P_STAGES], full_split[P_STAGES], empty[P_STAGES];
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int KB = (2 * Nc) / BK;
+  const int MT = (2 * Nc) / PM, NT = (ncol + BN - 1) / BN;
+  const int tiles = MT * NT * Nr;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < P_STAGES; ++s) {
+      mbar_init(&full_tma[s], 1);
+      mbar_init(&full_split[s], 256);                   // 128 split threads of each CTA (even CTA's copy is used)
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 256);                    // 128 epilogue threads of each CTA
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc_pair(&tmem_holder, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();                                       // the peer's barriers exist before any remote arrive
+  tc_fence_after();
+  const uint32_t tmem = tmem_holder;
+  volatile int* abort_p = &abort_flag;
+  auto stage_ptr = [&](int s) { return smem + (size_t)s * P_STAGE_BYTES; };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (both CTAs) ----------------
+      int g = 0;
+      bool ok = true;
+      for (int tile = pair; tile < tiles && ok; tile += npairs) {
+        const int mt = tile % MT, nt = (tile / MT) % NT, site = tile / (MT * NT);
+        const int row0 = mt * PM + (int)rank * BM;
+        // a half tile wholly past the last column loads columns 0.. instead (its
+        // products land in accumulator columns the epilogue never reads), so no
+        // box lies entirely outside the tensor
+        int col0 = nt * BN + (int)rank * (BN / 2);
+        col0 = col0 < ncol ? col0 : 0;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % P_STAGES;
+          if (g >= P_STAGES && !mbar_wait(&empty[s], ((g / P_STAGES) - 1) & 1, abort_p)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = stage_ptr(s);
+          mbar_expect_tx(&full_tma[s], P_TMA_BYTES);
+          tma_load_3d(st, &map_ahi, &full_tma[s], kb * BK, row0, site);
+          tma_load_3d(st + A_TILE, &map_alo, &full_tma[s], kb * BK, row0, site);
+          tma_load_3d(st + 2 * A_TILE, &map_xh, &full_tma[s], kb * BK, col0, site);
+          {
+            const int ahead = kb + PREFETCH;
+            const int t2 = ahead < KB ? tile : tile + npairs;
+            if (t2 < tiles && (ahead < KB || ahead - KB < KB)) {
+              const int k2 = ahead < KB ? ahead : ahead - KB;
+              const int m2 = t2 % MT, n2 = (t2 / MT) % NT, s2 = t2 / (MT * NT);
+              tma_prefetch_3d(&map_ahi, k2 * BK, m2 * PM + (int)rank * BM, s2);
+              tma_prefetch_3d(&map_alo, k2 * BK, m2 * PM + (int)rank * BM, s2);
+              const int c2 = n2 * BN + (int)rank * (BN / 2);
+              tma_prefetch_3d(&map_xh, k2 * BK, c2 < ncol ? c2 : 0, s2);
+            }
+          }
+        }
+      }
+      for (int q = g > P_STAGES ? g - P_STAGES : 0; q < g; ++q)
+        mbar_wait(&full_tma[q % P_STAGES], (q / P_STAGES) & 1, abort_p, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // ---------------- MMA issuer (even CTA only) ----------------
+      int g = 0, t = 0;
+      bool ok = true, any = false;
+      for (int tile = pair; tile < tiles && ok; tile += npairs, ++t) {
+        const int buf = t & 1;
+        if (t >= 2 && !mbar_wait_cluster(&acc_empty[buf], ((t >> 1) - 1) & 1, abort_p)) break;
+        tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(buf * ACC_COLS);
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % P_STAGES;
+          if (!mbar_wait_cluster(&full_split[s], (g / P_STAGES) & 1, abort_p)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = smem_u32(stage_ptr(s));
+          const uint32_t a_lo = a_hi + A_TILE;
+          const uint32_t x_hi = a_hi + 2 * A_TILE;
+          const uint32_t x_lo = x_hi + PX_TILE;
+#pragma unroll
+          for (int k8 = 0; k8 < BK / 8; ++k8) {
+            const uint32_t off = k8 * 32;
+            const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
+            const uint64_t dxh = sdesc_sw128(x_hi + off), dxl = sdesc_sw128(x_lo + off);
+            mma_pair_tf32(dacc, dah, dxh, P_IDESC, (kb | k8) ? 1u : 0u);
+            mma_pair_tf32(dacc, dah, dxl, P_IDESC, 1u);
+            mma_pair_tf32(dacc, dal, dxh, P_IDESC, 1u);
+          }
+          mma_commit_pair_mc(&empty[s], 0x3);
+          any = true;
+        }
+        if (ok) mma_commit_pair_mc(&acc_full[buf], 0x3);
+      }
+      if (any) {
+        mma_commit_pair_mc(&drain, 0x1);
+        mbar_wait(&drain, 0, abort_p, false);
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ---------------- split own half of X (both CTAs) ----------------
+    const int tt = threadIdx.x - 128;
+    const uint32_t split_bar0 = mapa(smem_u32(&full_split[0]), 0);
+    int g = 0;
+    bool ok = true;
+    for (int tile = pair; tile < tiles && ok; tile += npairs) {
+      for (int kb = 0; kb < KB; ++kb, ++g) {
+        const int s = g % P_STAGES;
+        if (!mbar_wait(&full_tma[s], (g / P_STAGES) & 1, abort_p)) {
+          ok = false;
+          break;
+        }
+        split_tile<PX_TILE>(stage_ptr(s) + 2 * A_TILE, tt);
+        fence_async_smem();
+        mbar_arrive_remote(split_bar0 + (uint32_t)(s * sizeof(uint64_t)));
+      }
+    }
+  } else if (warp >= 8) {
+    // ---------------- epilogue (both CTAs, own 128 rows) ----------------
+    const int q4 = warp - 8;
+    const size_t N2 = 2 * (size_t)Nc;
+    const uint32_t empty_bar0 = mapa(smem_u32(&acc_empty[0]), 0);
+    int t = 0;
+    for (int tile = pair; tile < tiles; tile += npairs, ++t) {
+      const int mt = tile % MT, nt = (tile / MT) % NT, site = tile / (MT * NT);
+      const int buf = t & 1;
+      bool go = mbar_wait(&acc_full[buf], (t >> 1) & 1, abort_p);
+      go = __all_sync(0xffffffffu, go);
+      if (!go) break;
+      tc_fence_after();
+      epilogue_rows(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS),
+                    mt * PM + (int)rank * BM + q4 * 32 + lane, nt * BN, site, ncol, gs, N2, r, din, dout, norm, lane);
+      tc_fence_before();
+      mbar_arrive_remote(empty_bar0 + (uint32_t)(buf * sizeof(uint64_t)));
+    }
+  }
+
+  // both CTAs stay resident until the even CTA's MMAs (which read the odd CTA's
+  // shared memory and write its TMEM) have drained and every remote arrive landed
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, TMEM_COLS);
   }
   if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
 }
@@ -362,14 +582,45 @@ TcState* state(dyson_ctx* c) {
   return static_cast<TcState*>(c->tc);
 }
 
+// co-resident CTA pairs of k_tc_gemm_pair on this device (0: the pair kernel cannot run)
+int pair_clusters(dyson_ctx* c, TcState* st) {
+  if (st->pair_clusters >= 0) return st->pair_clusters;
+  st->pair_clusters = 0;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) sms = 0;
+  if (sms >= 2 &&
+      cudaFuncSetAttribute(k_tc_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, P_SMEM_BYTES) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (unsigned)(sms / 2));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = P_SMEM_BYTES;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_tc_gemm_pair, &cfg) == cudaSuccess) st->pair_clusters = ncl;
+  }
+  cudaGetLastError();
+  return st->pair_clusters;
+}
+
 }  // namespace
+
+bool tc_uses_pair(dyson_ctx* c) {
+  return c->tc_variant == DYSON_SWEEP_CTA_PAIR && c->Nc % 128 == 0 && pair_clusters(c, state(c)) > 0;
+}
 
 bool tc_supported(dyson_ctx* c, int Nc) {
   (void)c;
   return Nc % 64 == 0 && encode_fn() != nullptr;
 }
 
-int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout) {
+int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, int phases) {
   TcState* st = state(c);
   const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;
   if (!st->d_err) {
@@ -408,14 +659,45 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
     DY_CUDA(c, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     st->smem_set = true;
   }
-  int gblocks = Nr * ((ncol + GATHER_COLS - 1) / GATHER_COLS);
-  k_tc_gather<<<gblocks, 256, 0, c->stream>>>(din, c->d_Jz, c->d_nbr, c->d_nbond, st->xbuf, Nr, Nc, ncol);
-  const long long tiles = (long long)(N2 / BM) * ((ncol + BN - 1) / BN) * Nr;
-  const int grid = (int)std::min<long long>(tiles, st->num_sms > 0 ? st->num_sms : 148);
-  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->a_hi, st->a_lo, st->x, r, din, dout, Nr, Nc, ncol, gs,
-                                                       c->d_norm, st->d_err);
+  const bool use_pair = tc_uses_pair(c);
+  if (phases & TC_GATHER) {
+    int gblocks = Nr * ((ncol + GATHER_COLS - 1) / GATHER_COLS);
+    k_tc_gather<<<gblocks, 256, 0, c->stream>>>(din, c->d_Jz, c->d_nbr, c->d_nbond, st->xbuf, Nr, Nc, ncol);
+    DY_CUDA(c, cudaGetLastError());
+    c->launches += 1;
+  }
+  if (!(phases & TC_GEMM)) return DYSON_OK;
+  if (use_pair) {
+    if (st->xh_ptr != st->xbuf || st->xh_ncol != ncol) {
+      if (!make_map(&st->xh, st->xbuf, N2, ncol, Nr, BN / 2))
+        return ctx_fail(c, DYSON_ERR_CUDA, "cuTensorMapEncodeTiled failed for X halves");
+      st->xh_ptr = st->xbuf;
+      st->xh_ncol = ncol;
+    }
+    const long long tiles = (long long)(N2 / PM) * ((ncol + BN - 1) / BN) * Nr;
+    const int pairs = (int)std::min<long long>(tiles, st->pair_clusters);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (unsigned)pairs);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = P_SMEM_BYTES;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    DY_CUDA(c, cudaLaunchKernelEx(&cfg, k_tc_gemm_pair, st->a_hi, st->a_lo, st->xh, r, din, dout, Nr, Nc, ncol, gs,
+                                  c->d_norm, st->d_err));
+  } else {
+    const long long tiles = (long long)(N2 / BM) * ((ncol + BN - 1) / BN) * Nr;
+    const int grid = (int)std::min<long long>(tiles, st->num_sms > 0 ? st->num_sms : 148);
+    k_tc_gemm<<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->a_hi, st->a_lo, st->x, r, din, dout, Nr, Nc, ncol, gs,
+                                                         c->d_norm, st->d_err);
+  }
   DY_CUDA(c, cudaGetLastError());
-  c->launches += 2;
+  c->launches += 1;
   return DYSON_OK;
 }
 

@@ -30,6 +30,7 @@ def _rel(a, b):
 CASES = [
     dict(L=3, Ly=2, Nt=7, Nm=5, trap_c=0.3, aU=0.1, aJ=0.2, omega=6.0),       # Nc = 19: CUDA-core paths
     dict(L=2, Ly=3, Nt=24, Nm=16, trap_c=0.3, U0=20.0, aU=0.1, aJ=0.2, omega=20.0),   # Nc = 64: tensor cores
+    dict(L=3, Ly=2, Nt=40, Nm=48, trap_c=0.2, U0=16.0, aU=0.1, aJ=0.2, omega=20.0),   # Nc = 128: CTA pairs
 ]
 
 
@@ -47,6 +48,7 @@ def test_vector_columns_and_rows_match_dense(torch_cuda, lib, kw, prec, transpos
         S = adjoint.transposed_setup(S)
     ref = dyson.dense_solve(S, dyson.rhs_vector_columns(S, list(zip(sites, times))))
     s = _solver(p)
+    s.set_sweep_variant(1)                                   # the CTA-pair form where Nc allows it
     if transposed:
         s.transpose_sigma()
     g = torch_cuda.empty((n, p.Nr, p.Nc), dtype=torch_cuda.complex128, device="cuda:0")

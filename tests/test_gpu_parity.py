@@ -98,10 +98,27 @@ def test_tensor_core_path_matches_dense(torch_cuda, lib, kw):
     s = _solver(p)
     s.profile(True)
     got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
-    launches, _ = s.profile_query(2)
-    assert launches > 0                                     # the tensor-core sweep ran
+    launches = s.profile_query(2)[0] + s.profile_query(5)[0]
+    assert launches > 0                                     # a tensor-core sweep ran
+    assert s.profile_query(5)[0] == 0                        # the single-CTA form is the default
     assert s.profile_query(4)[0] == res.report["refinements"] > 0   # every residual used BF16 slice products
     for q in range(len(sources)):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+
+
+def test_pair_kernel_ragged_column_tiles(torch_cuda, lib):
+    """Nc = 128 with the CTA-pair sweep selected.  Three block columns make 384
+    vector columns: the last 256-column tile has its odd CTA's half wholly past the end."""
+    p = wl.random_tables(wl.small(**TC_CASES[1]), seed=12, rel=0.2)
+    S = dyson.setup(p)
+    sources = [0, 3, 5]
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    s = _solver(p)
+    s.set_sweep_variant(1)
+    s.profile(True)
+    got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
+    assert s.profile_query(5)[0] > 0 and s.profile_query(2)[0] == 0
+    for q, i in enumerate(sources):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
 
