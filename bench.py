@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--f64-columns", type=int, default=2, help="block columns timed on the plain FP64 path")
     ap.add_argument("--cpu-columns", type=int, default=32, help="vector columns in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU legs (profiling runs)")
+    ap.add_argument("--uneven-instances", type=int, default=64,
+                    help="instances of the seeded uneven batch in the batched-solve leg (0 skips it)")
     ap.add_argument("--lattice", type=int, default=16,
                     help="lattice side; 16 is the benchmark workload, smaller sides serve ncu captures only")
     return ap.parse_args()
@@ -170,6 +172,56 @@ def cpu_baseline(p, ncols: int):
     return {"value": 1.0 / per_block, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
             "sample": (f"{ncols} of the 256 vector columns of block column 119, complex128 series to 1e-12 "
                        f"({sweeps} sweeps, {dt:.2f} s), scaled linearly to one block column")}
+
+
+def batched_uneven_leg(args, dev, stream):
+    """The seeded uneven batch (lattice sides 8..24, Nc in {128, 192, 256}, U, trap and
+    drive phase drawn per instance): one block column per instance (the site next to
+    the trap centre) solved to the same FP64 residual, once as one dyson_batch
+    (shared sweep launches under CUDA graphs) and once instance by instance."""
+    import torch
+    import workloads as wl
+    from paper_1309_5994_gb300 import binding
+    problems = wl.config4(count=args.uneven_instances)
+    solvers = []
+    for p in problems:
+        s = binding.Solver(p, device=dev.index, stream=stream)
+        s.build_sigma()
+        solvers.append(s)
+    sources = [[p.Nr // 2 + p.Lx // 2] for p in problems]
+    batch = binding.Batch(solvers)
+    # instances whose series diverges (spectral radius of Lambda W J above 1) end
+    # with DIVERGED; the paper hands those to GMRES, which this leg does not run
+    batch.solve(sources, tol=args.tol, allow=(0, -4))      # warm-up: tables, graph, buffers
+    torch.cuda.synchronize(dev)
+    l0 = batch.launch_count()
+    t0 = time.perf_counter()
+    res = batch.solve(sources, tol=args.tol, allow=(0, -4))
+    torch.cuda.synchronize(dev)
+    t_batch = time.perf_counter() - t0
+    graph_launches = batch.launch_count() - l0
+    t0 = time.perf_counter()
+    for s, src in zip(solvers, sources):
+        s.solve(src, precision=binding.PREC_TF32X3_F64REF, tol=args.tol, max_sweeps=400, allow=(0, -4))
+    torch.cuda.synchronize(dev)
+    t_seq = time.perf_counter() - t0
+    n = len(problems)
+    conv = [k for k, r in enumerate(res) if r.status == 0]
+    flops = sum(r.report["gemm_flops"] for r in res)
+    out = {"value": len(conv) / t_batch, "unit": UNIT, "instances": n, "block_columns_converged": len(conv),
+           "diverged_instances": [k for k, r in enumerate(res) if r.status == -4],
+           "value_note": "converged block columns per second of the whole batch (diverged instances' time included)",
+           "shapes": {"lattice_sides": sorted({p.Lx for p in problems}), "Nc": sorted({p.Nc for p in problems})},
+           "seconds": t_batch, "contour_gemm_tflops": flops / t_batch / 1e12,
+           "sequential_value": len(conv) / t_seq, "speedup_vs_sequential": t_seq / t_batch,
+           "sweeps_max": max(r.report["sweeps"] for r in res),
+           "refinements_max": max(r.report["refinements"] for r in res),
+           "max_rel_residual_converged": max(res[k].report["residual"] for k in conv) if conv else None,
+           "graph_kernel_launches": graph_launches, "tol_rel_residual": args.tol}
+    batch.close()
+    for s in solvers:
+        s.close()
+    return out
 
 
 def run_reference(args, rank, world):
@@ -357,6 +409,8 @@ def run_gb300(args, rank, world, local):
             del g64, gmx
             if world == 1:
                 extras["cpu_baseline"] = cpu_baseline(p, args.cpu_columns)
+            if args.uneven_instances > 0:
+                extras["batched_uneven"] = batched_uneven_leg(args, dev, stream)
 
     if rank != 0:
         return

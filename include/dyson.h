@@ -49,7 +49,10 @@ enum {
   DYSON_ERR_INVALID_ARG = -1,   /* a size, pointer or option is out of range            */
   DYSON_ERR_OOM = -2,           /* device allocation failed                              */
   DYSON_ERR_NOT_CONVERGED = -3, /* max_sweeps reached above tolerance (results written)  */
-  DYSON_ERR_DIVERGED = -4,      /* update or residual not finite or above 1e200          */
+  DYSON_ERR_DIVERGED = -4,      /* the series does not converge: the FP64 update passes  */
+                                /* 2^52 (rounding exceeds the result), an update or      */
+                                /* residual is not finite, or refinement residuals grow  */
+                                /* twice (spectral radius of Lambda W J above 1)         */
   DYSON_ERR_TIMEOUT = -5,       /* a bounded device wait expired                          */
   DYSON_ERR_CUDA = -6,          /* a CUDA runtime call failed                             */
   DYSON_ERR_STATE = -7          /* call order violated (e.g. solve before build_sigma)    */
@@ -213,6 +216,49 @@ int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);
  * unknown variant. */
 enum { DYSON_SWEEP_SINGLE_CTA = 0, DYSON_SWEEP_CTA_PAIR = 1 };
 int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
+
+/* ---------------------------------------------------------------------------
+ * Batched solves of several problem instances.  The paper solves one trap at a
+ * time; this entry point serves scans over many traps, lattices and drives.
+ * Each context keeps its own lattice, contour, trap, drive and Lambda, and its
+ * block columns are solved exactly as dyson_solve_columns(precision =
+ * DYSON_PREC_TF32X3_F64REF) solves them (the series of App. C refined with
+ * FP64-accurate residuals).  What the instances share is the inner FP32
+ * series.  Every sweep is ONE gather launch and ONE persistent tensor-core
+ * launch over the tiles of all instances still iterating, followed by a check
+ * kernel that applies each instance's stopping rule on the device.  Blocks of
+ * graph_sweeps sweeps are captured once as a CUDA graph and replayed with no
+ * host round trip inside a block.
+ *
+ * Requirements: every context is on the same device and stream, its Lambda is
+ * built and upright, and its contour suits the tensor-core path with the
+ * split-product residual (Nc a multiple of 64, Nc <= 256).  The block columns
+ * of one instance are solved as one chunk: DYSON_ERR_OOM if they do not fit.
+ *
+ * Ownership: the batch holds pointers to the contexts, not the contexts.
+ * Destroy the batch before its contexts.
+ * ------------------------------------------------------------------------- */
+typedef struct dyson_batch dyson_batch;
+enum { DYSON_BATCH_MAX_INSTANCES = 64 };
+
+/* Group n contexts (1 <= n <= DYSON_BATCH_MAX_INSTANCES, no duplicates) into a batch. */
+int dyson_batch_create(dyson_batch** out, dyson_ctx* const* ctxs, int32_t n);
+
+/* Solve the block columns src[k][0..n_src[k]) of instance k, for every k, to a
+ * relative FP64 Dyson residual <= tol; max_sweeps bounds each inner series.
+ * graph_sweeps = sweeps per graph replay (0 = 8; odd values are rounded up).
+ * g_out: NULL, or per instance NULL or a device buffer [n_src[k]][Nr][Nc][Nc]
+ * complex128 (the layout of dyson_solve_columns).  reports: NULL or n entries.
+ * Observables are read afterwards per context with dyson_observables.
+ * Returns the first non-OK instance status (NOT_CONVERGED, DIVERGED), or an
+ * error code; dyson_batch_last_error describes it. */
+int dyson_batch_solve(dyson_batch* b, const int32_t* const* src, const int32_t* n_src, double tol,
+                      int32_t max_sweeps, int32_t graph_sweeps, double* const* g_out, dyson_report* reports);
+
+/* Kernels launched by the batch's sweep graphs (3 per sweep; -1 for NULL). */
+int64_t dyson_batch_launch_count(const dyson_batch* b);
+const char* dyson_batch_last_error(const dyson_batch* b);
+void dyson_batch_destroy(dyson_batch* b);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free solve of one block column.  The paper has no counterpart:

@@ -55,7 +55,9 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_observables", "dyson_solve_vector_columns", "dyson_transpose_sigma", "dyson_adjoint",
            "dyson_profile", "dyson_profile_query", "dyson_set_chunk",
            "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
-           "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant"]
+           "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
+           "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
+           "dyson_batch_destroy"]
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
 
 
@@ -89,6 +91,15 @@ def load(path: str = _LIB_PATH):
                                                      C.c_double, C.c_int32, C.c_double, C.c_int32, P,
                                                      C.POINTER(C.c_int32), P]
     lib.dyson_noalloc_last_error.restype = C.c_char_p
+    lib.dyson_batch_create.argtypes = [C.POINTER(P), C.POINTER(P), C.c_int32]
+    lib.dyson_batch_solve.argtypes = [P, C.POINTER(C.POINTER(C.c_int32)), C.POINTER(C.c_int32), C.c_double,
+                                      C.c_int32, C.c_int32, C.POINTER(P), C.POINTER(Report)]
+    lib.dyson_batch_launch_count.argtypes = [P]
+    lib.dyson_batch_launch_count.restype = C.c_int64
+    lib.dyson_batch_last_error.argtypes = [P]
+    lib.dyson_batch_last_error.restype = C.c_char_p
+    lib.dyson_batch_destroy.argtypes = [P]
+    lib.dyson_batch_destroy.restype = None
     lib.dyson_destroy.argtypes = [P]
     lib.dyson_destroy.restype = None
     lib.dyson_last_error.argtypes = [P]
@@ -234,6 +245,62 @@ class Solver:
     def close(self):
         if getattr(self, "h", None):
             self.lib.dyson_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """dyson_batch over Solver objects that share one device and one stream.
+
+    solve() runs the mixed-precision solve of every instance's block columns
+    with shared sweep launches (see include/dyson.h); results per instance."""
+
+    def __init__(self, solvers):
+        self.lib = load()
+        self.solvers = list(solvers)
+        arr = (C.c_void_p * len(self.solvers))(*[sv.h for sv in self.solvers])
+        h = C.c_void_p()
+        rc = self.lib.dyson_batch_create(C.byref(h), arr, len(self.solvers))
+        if rc != 0:
+            raise DysonError(rc, self.lib.dyson_last_error(None).decode())
+        self.h = h
+
+    def solve(self, sources, tol=1e-10, max_sweeps=400, graph_sweeps=8, g_outs=None, allow=(0,)):
+        """sources[k]: block-column source sites of instance k; g_outs: None or per
+        instance None / a complex128 device tensor [len(sources[k]), Nr, Nc, Nc]."""
+        n = len(self.solvers)
+        assert len(sources) == n
+        keep = [np.ascontiguousarray(np.asarray(s, dtype=np.int32)) for s in sources]
+        ptrs = (C.POINTER(C.c_int32) * n)(*[k.ctypes.data_as(C.POINTER(C.c_int32)) for k in keep])
+        counts = (C.c_int32 * n)(*[len(k) for k in keep])
+        gp = None
+        if g_outs is not None:
+            vals = []
+            for sv, k, g in zip(self.solvers, keep, g_outs):
+                if g is None:
+                    vals.append(None)
+                    continue
+                assert g.is_cuda and g.dtype == sv._torch.complex128 and g.is_contiguous()
+                assert g.numel() == len(k) * sv.p.Nr * sv.p.Nc * sv.p.Nc
+                vals.append(g.data_ptr())
+            gp = (C.c_void_p * n)(*vals)
+        reps = (Report * n)()
+        rc = self.lib.dyson_batch_solve(self.h, ptrs, counts, tol, max_sweeps, graph_sweeps, gp, reps)
+        if rc not in allow:
+            raise DysonError(rc, self.lib.dyson_batch_last_error(self.h).decode())
+        return [SolveResult(r.status, r.as_dict()) for r in reps]
+
+    def launch_count(self) -> int:
+        return int(self.lib.dyson_batch_launch_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dyson_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -7,23 +7,13 @@
 #include <limits>
 
 #include "common.cuh"
+#include "detail.cuh"
 #include "oz.cuh"
 #include "tc.cuh"
 
-namespace {
+namespace dyson_detail {
 
 thread_local std::string g_noctx_err;
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int d) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    cudaSetDevice(d);
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 int fail_noctx(int code, const std::string& m) {
   g_noctx_err = m;
@@ -141,7 +131,6 @@ double rel_max(const unsigned long long* norm, const double* ref, int ng) {
   return m;
 }
 
-constexpr double kDivergedGrowth = 1e200;
 
 // algorithmic contour-GEMM flops of one sweep over ncol vector columns
 double sweep_flops(const dyson_ctx* c, int ncol) { return 8.0 * c->Nc * (double)c->Nc * c->Nr * ncol; }
@@ -161,6 +150,7 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
   if (rc) return rc;
   std::vector<double> scale(ng);
   for (int q = 0; q < ng; ++q) scale[q] = bits_to_double(c->h_norm[ng + q]);
+  *result = Ga;
   int status = DYSON_ERR_NOT_CONVERGED;
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
@@ -177,7 +167,7 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
     r->sweeps += 1;
     r->gemm_flops += sweep_flops(c, ncol);
     r->update = upd;
-    if (!(upd < kDivergedGrowth)) {
+    if (!(upd < kDivergedF64)) {
       status = DYSON_ERR_DIVERGED;
       break;
     }
@@ -222,10 +212,7 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
     rep->gemm_flops += sweep_flops(c, ncol);
     rep->update = upd;
     if (!(upd < kDivergedGrowth)) return ctx_fail(c, DYSON_ERR_DIVERGED, "FP32 series update not finite");
-    // The update first grows (transient of the real-time series), falls
-    // factorially after its peak, then settles at the FP32 rounding level of the
-    // partial sums.  Stop at 4e-7, or once it sits 1e-4 below its peak and has
-    // not improved for 4 sweeps.
+    // stopping rule of the inner series (detail.cuh)
     peak = std::max(peak, upd);
     if (upd < best) {
       best = upd;
@@ -233,8 +220,8 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
     } else {
       ++since_best;
     }
-    if (upd <= 4e-7) break;
-    if (since_best >= 4 && best < 1e-4 * peak) break;
+    if (upd <= kInnerTarget) break;
+    if (since_best >= kStallSweeps && best < kStallDrop * peak) break;
   }
   *dres = da;
   return DYSON_OK;
@@ -260,10 +247,19 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
   if ((rc = read_norms(c, ng, true))) return rc;
   std::vector<double> scale(ng), rref(ng);
   for (int q = 0; q < ng; ++q) rref[q] = scale[q] = bits_to_double(c->h_norm[ng + q]);
+  // the caller reads the chunk state (observables, export) whatever the status
+  *result = G;
   int status = DYSON_ERR_NOT_CONVERGED;
+  double prev_res = std::numeric_limits<double>::infinity();
+  int strikes = 0;
   for (int ref = 0; ref < c->max_refinements; ++ref) {
     float* d = nullptr;
-    if ((rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep))) return rc;
+    rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep);
+    if (rc == DYSON_ERR_DIVERGED) {
+      status = rc;
+      break;
+    }
+    if (rc) return rc;
     launch_accumulate(G, d, c->Nr, c->Nc, ncol, c->stream);
     c->launches += 1;
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
@@ -292,12 +288,18 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
       status = DYSON_OK;
       break;
     }
+    if (res > kRefineContract * prev_res && ++strikes >= kRefineStrikes) {
+      status = DYSON_ERR_DIVERGED;
+      break;
+    }
+    prev_res = res;
   }
-  *result = G;
   return status;
 }
 
-}  // namespace
+}  // namespace dyson_detail
+
+using namespace dyson_detail;
 
 int ctx_fail(dyson_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -424,7 +426,7 @@ int dyson_copy_sigma(dyson_ctx* c, double* dst, int on_device) {
 
 }  // extern "C"
 
-namespace {
+namespace dyson_detail {
 
 // Build the reduced-precision copies of Lambda a solve needs and pick the sweep
 // and residual kernels (sets c->use_tc, c->use_oz).
@@ -512,7 +514,7 @@ int fold_status(int status, int st) {
   return status;
 }
 
-}  // namespace
+}  // namespace dyson_detail
 
 extern "C" {
 
@@ -550,6 +552,7 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
     double2* G = nullptr;
     int st = solve_chunk(c, ncol, c->Nc, precision, tol, max_sweeps, &G, &R.rep);
     if (st != DYSON_OK && st != DYSON_ERR_NOT_CONVERGED && st != DYSON_ERR_DIVERGED) return R.finish(st);
+    if (!G) return R.finish(ctx_fail(c, DYSON_ERR_STATE, "solve produced no state"));
     status = fold_status(status, st);
     R.rep.chunks += 1;
     launch_observables(G, c->d_src_site, nq, c->d_nbr, c->d_nbond, c->dJ, c->d_eps, c->dU, c->Nr, c->Nt, c->Nc,
@@ -564,7 +567,7 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
   flush_timers(c);
   if (status == DYSON_ERR_NOT_CONVERGED) ctx_fail(c, status, "max_sweeps or refinement limit reached above tolerance");
-  if (status == DYSON_ERR_DIVERGED) ctx_fail(c, status, "series diverged (update not finite or above 1e200)");
+  if (status == DYSON_ERR_DIVERGED) ctx_fail(c, status, "series diverged (update not finite or past the rounding limit, or refinement residual growing)");
   return R.finish(status);
 }
 
@@ -600,6 +603,7 @@ int dyson_solve_vector_columns(dyson_ctx* c, const int32_t* sites, const int32_t
     double2* G = nullptr;
     int st = solve_chunk(c, ncol, GS, precision, tol, max_sweeps, &G, &R.rep);
     if (st != DYSON_OK && st != DYSON_ERR_NOT_CONVERGED && st != DYSON_ERR_DIVERGED) return R.finish(st);
+    if (!G) return R.finish(ctx_fail(c, DYSON_ERR_STATE, "solve produced no state"));
     status = fold_status(status, st);
     R.rep.chunks += 1;
     if (g_out) {
@@ -611,7 +615,7 @@ int dyson_solve_vector_columns(dyson_ctx* c, const int32_t* sites, const int32_t
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
   flush_timers(c);
   if (status == DYSON_ERR_NOT_CONVERGED) ctx_fail(c, status, "max_sweeps or refinement limit reached above tolerance");
-  if (status == DYSON_ERR_DIVERGED) ctx_fail(c, status, "series diverged (update not finite or above 1e200)");
+  if (status == DYSON_ERR_DIVERGED) ctx_fail(c, status, "series diverged (update not finite or past the rounding limit, or refinement residual growing)");
   return R.finish(status);
 }
 

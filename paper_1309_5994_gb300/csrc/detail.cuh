@@ -1,0 +1,59 @@
+// Host helpers of the solve drivers (capi.cu), shared with the batched driver (batch.cu).
+#pragma once
+#include <string>
+
+#include "common.cuh"
+
+namespace dyson_detail {
+
+// make device d current for the scope, restoring the previous device after
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// a relative update above this (or not finite) counts as divergence
+constexpr double kDivergedGrowth = 1e200;
+// An FP64 series whose relative update passes 2^52 has partial sums whose
+// rounding alone exceeds the result: it cannot converge to anything, and a
+// transient of the real-time series never comes near (about 2e7 on the longest
+// contours).  The FP64 series stops there with DYSON_ERR_DIVERGED.
+constexpr double kDivergedF64 = 4503599627370496.0;
+
+// Stopping rule of the FP32 inner series.  Its update first grows (the transient
+// of the real-time series), falls factorially after its peak, then settles at
+// the FP32 rounding level of the partial sums: stop at kInnerTarget, or once it
+// sits kStallDrop below its peak and has not improved for kStallSweeps sweeps.
+constexpr double kInnerTarget = 4e-7;
+constexpr double kStallDrop = 1e-4;
+constexpr int kStallSweeps = 4;
+
+// Refinement that grows the residual: a residual above kRefineContract times the
+// previous one, kRefineStrikes times, means the series of App. C does not
+// converge for this problem (spectral radius of K above 1); the solve ends with
+// DYSON_ERR_DIVERGED instead of spending its refinement budget.  A residual that
+// falls, however slowly, keeps the solve going (NOT_CONVERGED at the limit).
+constexpr double kRefineContract = 1.0;
+constexpr int kRefineStrikes = 2;
+
+int fail_noctx(int code, const std::string& m);           // error without a context
+double bits_to_double(unsigned long long b);
+void flush_timers(dyson_ctx* c);                          // fold finished event timings into the profile
+int ensure_work(dyson_ctx* c, size_t bytes);              // grow the work buffer
+int ensure_cols(dyson_ctx* c, int ncol, int ng);          // source arrays and norm words for a chunk
+int upload_sources(dyson_ctx* c, int ncol);               // host source arrays -> device
+int read_norms(dyson_ctx* c, int ng, bool with_scale);    // norm (and scale) words -> host, synchronises
+double rel_max(const unsigned long long* norm, const double* ref, int ng);
+double sweep_flops(const dyson_ctx* c, int ncol);         // algorithmic contour-GEMM flops of one sweep
+// reduced-precision copies of Lambda; sets c->use_tc, c->use_oz
+int prepare_tables(dyson_ctx* c, int precision);
+// vector columns per chunk that fit in device memory (multiple of unit, at most want)
+int64_t chunk_columns(dyson_ctx* c, int precision, int64_t unit, int64_t want, size_t* bytes_per_col);
+
+}  // namespace dyson_detail

@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 
 #include "ptx.cuh"
 #include "tc.cuh"
@@ -67,6 +68,10 @@ struct TcState {
   int xh_ncol = -1;
   const float* xh_ptr = nullptr;
   int pair_clusters = -1;
+  // one-entry instance table of the single-context sweep (pinned host copy and device copy)
+  TcInst* h_inst = nullptr;
+  TcInst* d_inst = nullptr;
+  bool inst_valid = false;
 };
 
 // Round to TF32 (10 explicit mantissa bits), to nearest with ties away from zero,
@@ -84,13 +89,30 @@ __device__ __forceinline__ unsigned long long nonneg_bits(float v) {
 
 // ---------------------------------------------------------------------------
 // gather: X[i][n][k] = sum_j J_ij(k mod Nc) d_j[n][k]
-// grid: one CTA per (block of 16 vector columns, site), column block outermost
+// grid: the instances' blocks back to back; within an instance one CTA per
+// (block of 16 vector columns, site), column block outermost
 // ---------------------------------------------------------------------------
 constexpr int GATHER_COLS = 16;
 
-__global__ __launch_bounds__(256) void k_tc_gather(const float* __restrict__ din, const float* __restrict__ Jz,
-                                                   const int* __restrict__ nbr, const int* __restrict__ nbond,
-                                                   float* __restrict__ X, int Nr, int Nc, int ncol) {
+// the instance whose range [key0, next key0) holds t (keys ascending, first key 0)
+template <int FIELD>
+__device__ __forceinline__ int find_inst(const TcInst* __restrict__ tab, int n, int t) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int key = FIELD == 0 ? tab[mid].tile0 : tab[mid].gblk0;
+    if (key <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool inst_active(const TcInst& I) { return I.active == nullptr || *I.active != 0; }
+
+// single instance: pointers and sizes as kernel parameters (32 registers, 8 blocks per SM)
+__global__ __launch_bounds__(256) void k_tc_gather_one(const float* __restrict__ din, const float* __restrict__ Jz,
+                                                       const int* __restrict__ nbr, const int* __restrict__ nbond,
+                                                       float* __restrict__ X, int Nr, int Nc, int ncol) {
   const int i = blockIdx.x % Nr;
   const int nblk = blockIdx.x / Nr;
   const int N2 = 2 * Nc;
@@ -119,6 +141,58 @@ __global__ __launch_bounds__(256) void k_tc_gather(const float* __restrict__ din
       acc.w = fmaf(j.w, g.w, acc.w);
     }
     *reinterpret_cast<float4*>(X + ((size_t)i * ncol + n) * N2 + k) = acc;
+  }
+}
+
+// batched: the instance table; an instance's blocks follow the previous instance's
+__global__ __launch_bounds__(256) void k_tc_gather(const TcInst* __restrict__ tab, int ninst, int parity) {
+  // the instance's pointers and this site's neighbours, read once per block
+  __shared__ const float* s_din;
+  __shared__ const float* s_Jz;
+  __shared__ float* s_X;
+  __shared__ int s_nb[4], s_bd[4], s_dim[4];
+  if (threadIdx.x == 0) {
+    const TcInst& I = tab[find_inst<1>(tab, ninst, blockIdx.x)];
+    const bool act = inst_active(I);
+    const int b = blockIdx.x - I.gblk0;
+    const int i = b % I.Nr;
+    s_din = I.buf[parity];
+    s_Jz = I.Jz;
+    s_X = I.X;
+    s_dim[0] = act ? I.Nc : 0;
+    s_dim[1] = I.ncol;
+    s_dim[2] = i;
+    s_dim[3] = b / I.Nr;
+    for (int q = 0; q < 4; ++q) {
+      s_nb[q] = I.nbr[i * 4 + q];
+      s_bd[q] = I.nbond[i * 4 + q];
+    }
+  }
+  __syncthreads();
+  const int Nc = s_dim[0];
+  if (Nc == 0) return;                                  // converged instance
+  const int ncol = s_dim[1], i = s_dim[2], nblk = s_dim[3];
+  const int N2 = 2 * Nc;
+  const int per_col4 = N2 / 4;
+  const int total4 = GATHER_COLS * per_col4;
+  for (int e = threadIdx.x; e < total4; e += blockDim.x) {
+    int c = e / per_col4, k = (e - c * per_col4) * 4;
+    int n = nblk * GATHER_COLS + c;
+    if (n >= ncol) break;
+    int kz = k < Nc ? k : k - Nc;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int nb = s_nb[s];
+      if (nb < 0) continue;
+      float4 j = *reinterpret_cast<const float4*>(s_Jz + (size_t)s_bd[s] * Nc + kz);
+      float4 g = *reinterpret_cast<const float4*>(s_din + ((size_t)nb * ncol + n) * N2 + k);
+      acc.x = fmaf(j.x, g.x, acc.x);
+      acc.y = fmaf(j.y, g.y, acc.y);
+      acc.z = fmaf(j.z, g.z, acc.z);
+      acc.w = fmaf(j.w, g.w, acc.w);
+    }
+    *reinterpret_cast<float4*>(s_X + ((size_t)i * ncol + n) * N2 + k) = acc;
   }
 }
 
@@ -187,13 +261,35 @@ __device__ __forceinline__ void epilogue_rows(uint32_t tacc, int mg, int n_first
 }
 
 // ---------------------------------------------------------------------------
-// persistent GEMM + epilogue
+// persistent GEMM + epilogue over the tiles of every instance of the table
 // ---------------------------------------------------------------------------
+// One 128 x 256 output tile of an instance, as every warp role decodes it.
+struct TileRef {
+  const TcInst* I;
+  int k;                             // instance index (its tensor maps are maps.*[k])
+  int KB, mt, nt, site;
+  bool active;
+};
+
+__device__ __forceinline__ TileRef decode_tile(const TcInst* __restrict__ tab, int ninst, int tile) {
+  TileRef T;
+  T.k = find_inst<0>(tab, ninst, tile);
+  T.I = &tab[T.k];
+  const int Nc = T.I->Nc;
+  const int MT = (2 * Nc) / BM, NT = (T.I->ncol + BN - 1) / BN;
+  const int lt = tile - T.I->tile0;
+  T.KB = (2 * Nc) / BK;
+  T.mt = lt % MT;
+  T.nt = (lt / MT) % NT;
+  T.site = lt / (MT * NT);
+  T.active = inst_active(*T.I);
+  return T;
+}
+
+template <int MAXI>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
-              const __grid_constant__ CUtensorMap map_x, const float* __restrict__ r, const float* __restrict__ din,
-              float* __restrict__ dout, int Nr, int Nc, int ncol, int gs, unsigned long long* __restrict__ norm,
-              int* __restrict__ err) {
+    k_tc_gemm(const __grid_constant__ TcMaps<MAXI> maps, const TcInst* __restrict__ tab, int ninst, int tiles,
+              int parity, int* __restrict__ err) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -203,9 +299,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int KB = (2 * Nc) / BK;
-  const int MT = (2 * Nc) / BM, NT = (ncol + BN - 1) / BN;
-  const int tiles = MT * NT * Nr;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -235,8 +328,20 @@ __global__ void __launch_bounds__(THREADS, 1)
       int g = 0;                                        // k-blocks issued by this CTA
       bool ok = true;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const int mt = tile % MT, nt = (tile / MT) % NT, site = tile / (MT * NT);
-        for (int kb = 0; kb < KB; ++kb, ++g) {
+        const TileRef T = decode_tile(tab, ninst, tile);
+        if (!T.active) continue;
+        const CUtensorMap* ma_hi = &maps.a_hi[T.k];
+        const CUtensorMap* ma_lo = &maps.a_lo[T.k];
+        const CUtensorMap* mx = &maps.x[T.k];
+        // the next active tile of this CTA, for the L2 prefetch that runs ahead of the loads
+        int t2 = tile + (int)gridDim.x;
+        TileRef N;
+        N.active = false;
+        for (; t2 < tiles; t2 += gridDim.x) {
+          N = decode_tile(tab, ninst, t2);
+          if (N.active) break;
+        }
+        for (int kb = 0; kb < T.KB; ++kb, ++g) {
           const int s = g % STAGES;
           if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1, abort_p)) {
             ok = false;
@@ -244,21 +349,21 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           uint8_t* st = stage_ptr(s);
           mbar_expect_tx(&full_tma[s], TMA_BYTES);
-          tma_load_3d(st, &map_ahi, &full_tma[s], kb * BK, mt * BM, site);
-          tma_load_3d(st + A_TILE, &map_alo, &full_tma[s], kb * BK, mt * BM, site);
-          tma_load_3d(st + 2 * A_TILE, &map_x, &full_tma[s], kb * BK, nt * BN, site);
+          tma_load_3d(st, ma_hi, &full_tma[s], kb * BK, T.mt * BM, T.site);
+          tma_load_3d(st + A_TILE, ma_lo, &full_tma[s], kb * BK, T.mt * BM, T.site);
+          tma_load_3d(st + 2 * A_TILE, mx, &full_tma[s], kb * BK, T.nt * BN, T.site);
           // warm L2 with the tiles of the k-block PREFETCH steps ahead: the stage
           // loads then see L2 latency instead of DRAM latency
-          {
-            const int ahead = kb + PREFETCH;
-            const int t2 = ahead < KB ? tile : tile + (int)gridDim.x;
-            if (t2 < tiles && (ahead < KB || ahead - KB < KB)) {
-              const int k2 = ahead < KB ? ahead : ahead - KB;
-              const int m2 = t2 % MT, n2 = (t2 / MT) % NT, s2 = t2 / (MT * NT);
-              tma_prefetch_3d(&map_ahi, k2 * BK, m2 * BM, s2);
-              tma_prefetch_3d(&map_alo, k2 * BK, m2 * BM, s2);
-              tma_prefetch_3d(&map_x, k2 * BK, n2 * BN, s2);
-            }
+          const int ahead = kb + PREFETCH;
+          if (ahead < T.KB) {
+            tma_prefetch_3d(ma_hi, ahead * BK, T.mt * BM, T.site);
+            tma_prefetch_3d(ma_lo, ahead * BK, T.mt * BM, T.site);
+            tma_prefetch_3d(mx, ahead * BK, T.nt * BN, T.site);
+          } else if (N.active && ahead - T.KB < N.KB) {
+            const int k2 = ahead - T.KB;
+            tma_prefetch_3d(&maps.a_hi[N.k], k2 * BK, N.mt * BM, N.site);
+            tma_prefetch_3d(&maps.a_lo[N.k], k2 * BK, N.mt * BM, N.site);
+            tma_prefetch_3d(&maps.x[N.k], k2 * BK, N.nt * BN, N.site);
           }
         }
       }
@@ -271,12 +376,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       // ---------------- MMA issuer ----------------
       int g = 0, t = 0;
       bool ok = true, any = false;
-      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const TileRef T = decode_tile(tab, ninst, tile);
+        if (!T.active) continue;
         const int buf = t & 1;
         if (t >= 2 && !mbar_wait(&acc_empty[buf], ((t >> 1) - 1) & 1, abort_p)) break;
+        ++t;
         tc_fence_after();
         const uint32_t dacc = tmem + (uint32_t)(buf * ACC_COLS);
-        for (int kb = 0; kb < KB; ++kb, ++g) {
+        for (int kb = 0; kb < T.KB; ++kb, ++g) {
           const int s = g % STAGES;
           if (!mbar_wait(&full_split[s], (g / STAGES) & 1, abort_p)) {
             ok = false;
@@ -312,7 +420,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     int g = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-      for (int kb = 0; kb < KB; ++kb, ++g) {
+      const TileRef T = decode_tile(tab, ninst, tile);
+      if (!T.active) continue;
+      for (int kb = 0; kb < T.KB; ++kb, ++g) {
         const int s = g % STAGES;
         if (!mbar_wait(&full_tma[s], (g / STAGES) & 1, abort_p)) {
           ok = false;
@@ -326,17 +436,20 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp >= 8) {
     // ---------------- epilogue ----------------
     const int q4 = warp - 8;                            // TMEM lane quarter (warp % 4)
-    const size_t N2 = 2 * (size_t)Nc;
     int t = 0;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++t) {
-      const int mt = tile % MT, nt = (tile / MT) % NT, site = tile / (MT * NT);
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      const TileRef T = decode_tile(tab, ninst, tile);
+      if (!T.active) continue;
       const int buf = t & 1;
       bool go = mbar_wait(&acc_full[buf], (t >> 1) & 1, abort_p);
+      ++t;
       go = __all_sync(0xffffffffu, go);                 // tcgen05.ld below is warp-collective
       if (!go) break;
       tc_fence_after();
-      epilogue_rows(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS), mt * BM + q4 * 32 + lane,
-                    nt * BN, site, ncol, gs, N2, r, din, dout, norm, lane);
+      const TcInst& I = *T.I;
+      epilogue_rows(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS), T.mt * BM + q4 * 32 + lane,
+                    T.nt * BN, T.site, I.ncol, I.gs, 2 * (size_t)I.Nc, I.r, I.buf[parity], I.buf[parity ^ 1],
+                    I.norm, lane);
       // this accumulator may be overwritten by the MMAs of tile t + 2
       tc_fence_before();
       mbar_arrive(&acc_empty[buf]);
@@ -620,7 +733,10 @@ bool tc_supported(dyson_ctx* c, int Nc) {
   return Nc % 64 == 0 && encode_fn() != nullptr;
 }
 
-int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, int phases) {
+namespace {
+
+// tensor maps of Lambda and the gather buffer of context c for ncol columns
+int tc_prepare(dyson_ctx* c, int ncol) {
   TcState* st = state(c);
   const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;
   if (!st->d_err) {
@@ -635,6 +751,7 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
     st->a_lo_ptr = c->d_lam_lo;
     st->a_Nr = Nr;
     st->a_Nc = Nc;
+    st->inst_valid = false;
   }
   size_t xbytes = (size_t)Nr * ncol * N2 * sizeof(float);
   if (st->xbuf_bytes < xbytes) {
@@ -654,20 +771,104 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
       return ctx_fail(c, DYSON_ERR_CUDA, "cuTensorMapEncodeTiled failed for X");
     st->x_ptr = st->xbuf;
     st->x_ncol = ncol;
+    st->inst_valid = false;
   }
   if (!st->smem_set) {
-    DY_CUDA(c, cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    DY_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    DY_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<TC_MAX_INSTANCES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES));
     st->smem_set = true;
   }
-  const bool use_pair = tc_uses_pair(c);
+  return DYSON_OK;
+}
+
+}  // namespace
+
+int tc_fill_instance(dyson_ctx* c, int ncol, int gs, const float* r, float* buf0, float* buf1,
+                     unsigned long long* norm, const int* active, TcInst* e, CUtensorMap* a_hi, CUtensorMap* a_lo,
+                     CUtensorMap* x) {
+  int rc = tc_prepare(c, ncol);
+  if (rc) return rc;
+  TcState* st = state(c);
+  std::memset(static_cast<void*>(e), 0, sizeof(TcInst));
+  *a_hi = st->a_hi;
+  *a_lo = st->a_lo;
+  *x = st->x;
+  e->r = r;
+  e->buf[0] = buf0;
+  e->buf[1] = buf1;
+  e->X = st->xbuf;
+  e->Jz = c->d_Jz;
+  e->nbr = c->d_nbr;
+  e->nbond = c->d_nbond;
+  e->norm = norm;
+  e->active = active;
+  e->Nr = c->Nr;
+  e->Nc = c->Nc;
+  e->ncol = ncol;
+  e->gs = gs;
+  return DYSON_OK;
+}
+
+int tc_instance_tiles(const TcInst& e) { return (2 * e.Nc / BM) * ((e.ncol + BN - 1) / BN) * e.Nr; }
+int tc_instance_gather_blocks(const TcInst& e) { return e.Nr * ((e.ncol + GATHER_COLS - 1) / GATHER_COLS); }
+
+namespace {
+
+template <int MAXI>
+int launch_gemm(dyson_ctx* c, const CUtensorMap* a_hi, const CUtensorMap* a_lo, const CUtensorMap* x,
+                const TcInst* d_tab, int ninst, int tiles, int parity, cudaStream_t stream) {
+  TcState* st = state(c);
+  static_assert(sizeof(TcMaps<MAXI>) <= 30000, "tensor maps exceed the kernel-parameter space");
+  TcMaps<MAXI> maps;
+  for (int k = 0; k < ninst; ++k) {
+    maps.a_hi[k] = a_hi[k];
+    maps.a_lo[k] = a_lo[k];
+    maps.x[k] = x[k];
+  }
+  const int grid = std::min(tiles, st->num_sms > 0 ? st->num_sms : 148);
+  k_tc_gemm<MAXI><<<grid, THREADS, SMEM_BYTES, stream>>>(maps, d_tab, ninst, tiles, parity, st->d_err);
+  return DYSON_OK;
+}
+
+}  // namespace
+
+int tc_launch_table(dyson_ctx* c, const TcInst* d_tab, int ninst, int tiles, int gblocks, int parity, int phases,
+                    cudaStream_t stream, const CUtensorMap* a_hi, const CUtensorMap* a_lo, const CUtensorMap* x,
+                    const TcInst* h_one) {
+  if (ninst < 1 || ninst > TC_MAX_INSTANCES)
+    return ctx_fail(c, DYSON_ERR_INVALID_ARG, "instance table of 1.." + std::to_string(TC_MAX_INSTANCES) + " entries");
+  TcState* st = state(c);
   if (phases & TC_GATHER) {
-    int gblocks = Nr * ((ncol + GATHER_COLS - 1) / GATHER_COLS);
-    k_tc_gather<<<gblocks, 256, 0, c->stream>>>(din, c->d_Jz, c->d_nbr, c->d_nbond, st->xbuf, Nr, Nc, ncol);
+    if (h_one && ninst == 1)
+      k_tc_gather_one<<<gblocks, 256, 0, stream>>>(h_one->buf[parity], h_one->Jz, h_one->nbr, h_one->nbond, h_one->X,
+                                                   h_one->Nr, h_one->Nc, h_one->ncol);
+    else
+      k_tc_gather<<<gblocks, 256, 0, stream>>>(d_tab, ninst, parity);
     DY_CUDA(c, cudaGetLastError());
     c->launches += 1;
   }
-  if (!(phases & TC_GEMM)) return DYSON_OK;
-  if (use_pair) {
+  if (phases & TC_GEMM) {
+    int rc = ninst == 1 ? launch_gemm<1>(c, a_hi, a_lo, x, d_tab, ninst, tiles, parity, stream)
+                        : launch_gemm<TC_MAX_INSTANCES>(c, a_hi, a_lo, x, d_tab, ninst, tiles, parity, stream);
+    if (rc) return rc;
+    DY_CUDA(c, cudaGetLastError());
+    c->launches += 1;
+  }
+  return DYSON_OK;
+}
+
+int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, int phases) {
+  int rc = tc_prepare(c, ncol);
+  if (rc) return rc;
+  TcState* st = state(c);
+  const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;
+  if (!(phases & TC_TABLE_ONLY) && tc_uses_pair(c)) {
+    if (phases & TC_GATHER) {
+      // the one-entry table serves the gather of the pair form too
+      if ((rc = tc_sweep(c, ncol, gs, r, din, dout, TC_GATHER | TC_TABLE_ONLY))) return rc;
+    }
+    if (!(phases & TC_GEMM)) return DYSON_OK;
     if (st->xh_ptr != st->xbuf || st->xh_ncol != ncol) {
       if (!make_map(&st->xh, st->xbuf, N2, ncol, Nr, BN / 2))
         return ctx_fail(c, DYSON_ERR_CUDA, "cuTensorMapEncodeTiled failed for X halves");
@@ -690,15 +891,34 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
     cfg.numAttrs = 1;
     DY_CUDA(c, cudaLaunchKernelEx(&cfg, k_tc_gemm_pair, st->a_hi, st->a_lo, st->xh, r, din, dout, Nr, Nc, ncol, gs,
                                   c->d_norm, st->d_err));
-  } else {
-    const long long tiles = (long long)(N2 / BM) * ((ncol + BN - 1) / BN) * Nr;
-    const int grid = (int)std::min<long long>(tiles, st->num_sms > 0 ? st->num_sms : 148);
-    k_tc_gemm<<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->a_hi, st->a_lo, st->x, r, din, dout, Nr, Nc, ncol, gs,
-                                                         c->d_norm, st->d_err);
+    DY_CUDA(c, cudaGetLastError());
+    c->launches += 1;
+    return DYSON_OK;
   }
-  DY_CUDA(c, cudaGetLastError());
-  c->launches += 1;
-  return DYSON_OK;
+  // one-entry table; the two states keep their slots, the parity says which is d_in
+  if (!st->h_inst) {
+    DY_CUDA(c, cudaMallocHost((void**)&st->h_inst, sizeof(TcInst)));
+    DY_CUDA(c, cudaMalloc((void**)&st->d_inst, sizeof(TcInst)));
+    st->inst_valid = false;
+  }
+  TcInst* h = st->h_inst;
+  int parity = -1;
+  if (st->inst_valid && h->r == r && h->ncol == ncol && h->gs == gs && h->norm == c->d_norm) {
+    if (h->buf[0] == din && h->buf[1] == dout) parity = 0;
+    else if (h->buf[1] == din && h->buf[0] == dout) parity = 1;
+  }
+  if (parity < 0) {
+    // the previous launches may still read the table: refill it behind them on the stream
+    DY_CUDA(c, cudaStreamSynchronize(c->stream));
+    CUtensorMap m0, m1, m2;
+    if ((rc = tc_fill_instance(c, ncol, gs, r, const_cast<float*>(din), dout, c->d_norm, nullptr, h, &m0, &m1, &m2)))
+      return rc;
+    DY_CUDA(c, cudaMemcpyAsync(st->d_inst, h, sizeof(TcInst), cudaMemcpyHostToDevice, c->stream));
+    st->inst_valid = true;
+    parity = 0;
+  }
+  return tc_launch_table(c, st->d_inst, 1, tc_instance_tiles(*h), tc_instance_gather_blocks(*h), parity,
+                         phases & (TC_GATHER | TC_GEMM), c->stream, &st->a_hi, &st->a_lo, &st->x, h);
 }
 
 int tc_check_error(dyson_ctx* c) {
@@ -719,6 +939,8 @@ void tc_release(dyson_ctx* c) {
   if (!st) return;
   if (st->xbuf) cudaFree(st->xbuf);
   if (st->d_err) cudaFree(st->d_err);
+  if (st->h_inst) cudaFreeHost(st->h_inst);
+  if (st->d_inst) cudaFree(st->d_inst);
   delete st;
   c->tc = nullptr;
 }

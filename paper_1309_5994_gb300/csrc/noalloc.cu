@@ -217,7 +217,7 @@ extern "C" int dyson_solve_block_column_noalloc(const double* lambda, const doub
     std::swap(cur, other);
     sweeps = sw;
     double upd = bits_to_d(h[0]) / scale;
-    if (!(upd < 1e200)) {
+    if (!(upd < 4503599627370496.0)) {        // 2^52: partial-sum rounding exceeds the result
       status = DYSON_ERR_DIVERGED;
       break;
     }

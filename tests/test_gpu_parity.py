@@ -175,6 +175,29 @@ def test_slow_series_reports_not_converged(torch_cuda, lib):
     assert np.all(np.isfinite(n[:2]))
 
 
+DIVERGENT = dict(L=3, Ly=3, Nt=24, Nm=16, dt=0.05, beta=2.0, trap_c=0.0, U0=4.0, J0=2.0)   # rho(K) = 1.41
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_divergent_series_reports_diverged(torch_cuda, lib, prec):
+    """J/U = 1/2: the spectral radius of K is 1.41, so the series of App. C
+    diverges.  Both paths must report DIVERGED, keep the context usable and leave
+    the CUDA context clean (no launch on a missing state)."""
+    torch = torch_cuda
+    from paper_1309_5994_gb300 import binding
+    p = wl.small(**DIVERGENT)
+    S = dyson.setup(p)
+    assert np.abs(np.linalg.eigvals(dyson.dense_K(S))).max() > 1.3
+    s = _solver(p)
+    g = torch.empty((1, p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda:0")
+    res = s.solve([4], precision=prec, tol=1e-12, max_sweeps=400, g_out=g, allow=(-4,))
+    assert res.status == -4
+    s.observables()                                          # the context still answers
+    torch.cuda.synchronize()
+    ok = _solver(wl.small(**SMALL[0]))
+    assert ok.solve([0], precision=prec, tol=1e-12).status == 0
+
+
 def test_config3_sampled_columns_fp64(torch_cuda, lib):
     """32x32 lattice, driven, Nc = 384: one block column in FP64, sampled vector
     columns against the oracle's complex128 series run for the same 130 sweeps.
