@@ -99,6 +99,9 @@ typedef struct {
                                    block column and sweep, over every sweep performed      */
   double seconds;               /* wall time of the call                                   */
   int64_t kernel_launches;      /* CUDA kernels this call launched                         */
+  int32_t inner_gmres;          /* 1 if a refinement used the GMRES inner solver (its      */
+                                /* matvecs are counted in sweeps), else 0                  */
+  int32_t reserved;
 } dyson_report;
 
 /* Create a context on `device`, ordering work on `cuda_stream` (a cudaStream_t,
@@ -216,6 +219,22 @@ int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);
  * unknown variant. */
 enum { DYSON_SWEEP_SINGLE_CTA = 0, DYSON_SWEEP_CTA_PAIR = 1 };
 int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
+
+/* Inner solver of the mixed-precision path (DYSON_PREC_TF32X3_F64REF), between
+ * FP64 residual refinements:
+ *   SERIES  the series of App. C in FP32;
+ *   GMRES   the preconditioned GMRES of App. C (preconditioner Lambda, the
+ *           block-diagonal B^-1; initial guess the preconditioned right-hand
+ *           side), restarted every `restart` iterations (0 = 40; at most 60,
+ *           and fewer when the Krylov basis does not fit in free memory);
+ *   AUTO    (the default) the series, switching to GMRES for the rest of a chunk
+ *           when the series diverges, its transient peak leaves FP32 no correct
+ *           digit (long contours), or the refined residual grows.
+ * GMRES keeps restart + 4 FP32 chunk states (8 Nr Nc bytes per vector column
+ * each).  The FP64 path (DYSON_PREC_F64) always runs the series.
+ * Returns INVALID_ARG for an unknown solver or a restart outside 0..60. */
+enum { DYSON_INNER_SERIES = 0, DYSON_INNER_GMRES = 1, DYSON_INNER_AUTO = 2 };
+int dyson_set_inner_solver(dyson_ctx* ctx, int solver, int32_t restart);
 
 /* ---------------------------------------------------------------------------
  * Batched solves of several problem instances.  The paper solves one trap at a

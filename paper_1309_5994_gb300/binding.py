@@ -45,7 +45,8 @@ class Drive(C.Structure):
 class Report(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("refinements", C.c_int32), ("chunks", C.c_int32),
                 ("status", C.c_int32), ("update", C.c_double), ("residual", C.c_double),
-                ("gemm_flops", C.c_double), ("seconds", C.c_double), ("kernel_launches", C.c_int64)]
+                ("gemm_flops", C.c_double), ("seconds", C.c_double), ("kernel_launches", C.c_int64),
+                ("inner_gmres", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -57,7 +58,8 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
-           "dyson_batch_destroy"]
+           "dyson_batch_destroy", "dyson_set_inner_solver"]
+INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
 
 
@@ -85,6 +87,7 @@ def load(path: str = _LIB_PATH):
     lib.dyson_profile_query.argtypes = [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     lib.dyson_set_chunk.argtypes = [P, C.c_int32]
     lib.dyson_set_sweep_variant.argtypes = [P, C.c_int]
+    lib.dyson_set_inner_solver.argtypes = [P, C.c_int, C.c_int32]
     lib.dyson_launch_count.argtypes = [P]
     lib.dyson_launch_count.restype = C.c_int64
     lib.dyson_solve_block_column_noalloc.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
@@ -229,6 +232,9 @@ class Solver:
 
     def set_chunk(self, cols: int):
         self._check(self.lib.dyson_set_chunk(self.h, cols))
+
+    def set_inner_solver(self, solver: int, restart: int = 0):
+        self._check(self.lib.dyson_set_inner_solver(self.h, solver, restart))
 
     def set_sweep_variant(self, variant: int):
         self._check(self.lib.dyson_set_sweep_variant(self.h, variant))

@@ -68,8 +68,11 @@ __global__ void k_batch_check(const BatchCheck* __restrict__ chk, int n, int* __
       S.diverged = 1;
       stop = true;
     } else {
-      S.peak = fmax(S.peak, upd);
-      if (upd < S.best) {
+      if (upd > S.peak) {                              // the stall is judged on the decay after the peak
+        S.peak = upd;
+        S.best = upd;
+        S.since_best = 0;
+      } else if (upd < S.best) {
         S.best = upd;
         S.since_best = 0;
       } else {

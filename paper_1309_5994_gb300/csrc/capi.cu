@@ -8,6 +8,7 @@
 
 #include "common.cuh"
 #include "detail.cuh"
+#include "gmres.cuh"
 #include "oz.cuh"
 #include "tc.cuh"
 
@@ -182,7 +183,8 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
 
 // inner solve d <- r + K d in FP32 (SIMT or 3xTF32 tensor cores)
 int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float* da, float* db, int max_sweeps,
-                const std::vector<double>& rref, float** dres, dyson_report* rep) {
+                const std::vector<double>& rref, float** dres, dyson_report* rep, double* peak_out,
+                double abort_peak = std::numeric_limits<double>::infinity()) {
   const int ng = ncol / gs;
   const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
   DY_CUDA(c, cudaMemcpyAsync(da, r32, n32 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
@@ -212,18 +214,47 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
     rep->gemm_flops += sweep_flops(c, ncol);
     rep->update = upd;
     if (!(upd < kDivergedGrowth)) return ctx_fail(c, DYSON_ERR_DIVERGED, "FP32 series update not finite");
-    // stopping rule of the inner series (detail.cuh)
-    peak = std::max(peak, upd);
-    if (upd < best) {
+    // stopping rule of the inner series (detail.cuh); the stall is judged only on
+    // the decay after the latest peak
+    if (upd > peak) {
+      peak = upd;
+      best = upd;
+      since_best = 0;
+    } else if (upd < best) {
       best = upd;
       since_best = 0;
     } else {
       ++since_best;
     }
+    if (peak > abort_peak) {
+      if (peak_out) *peak_out = peak;
+      return DYSON_ERR_DIVERGED;                           // the caller switches to GMRES
+    }
     if (upd <= kInnerTarget) break;
     if (since_best >= kStallSweeps && best < kStallDrop * peak) break;
   }
   *dres = da;
+  if (peak_out) *peak_out = peak;
+  return DYSON_OK;
+}
+
+// out = zero + K in: one FP32 sweep with a zero right-hand side (the GMRES matvec)
+int matvec_f32(dyson_ctx* c, int ncol, int gs, int precision, const float* zero, const float* in, float* out) {
+  int rc;
+  if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
+    {
+      KernelTimer t(c, DYSON_KERNEL_GATHER_TC);
+      if ((rc = tc_sweep(c, ncol, gs, zero, in, out, TC_GATHER))) return rc;
+    }
+    KernelTimer t(c, tc_uses_pair(c) ? DYSON_KERNEL_SWEEP_TC_PAIR : DYSON_KERNEL_SWEEP_TC);
+    if ((rc = tc_sweep(c, ncol, gs, zero, in, out, TC_GEMM))) return rc;
+  } else {
+    KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
+    launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, zero, in, out, c->Nr, c->Nc, ncol, gs,
+                          c->d_norm, c->stream);
+    c->launches += 1;
+  }
+  DY_CUDA(c, cudaGetLastError());
   return DYSON_OK;
 }
 
@@ -252,9 +283,31 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
   int status = DYSON_ERR_NOT_CONVERGED;
   double prev_res = std::numeric_limits<double>::infinity();
   int strikes = 0;
+  // inner solver: the series of App. C, or its GMRES.  AUTO starts with the series
+  // and switches to GMRES for the rest of the chunk when the series cannot serve:
+  // it diverges, its transient peak times the FP32 rounding leaves no correct
+  // digit, or the refined residual grows.
+  bool gmres = c->inner_solver == DYSON_INNER_GMRES;
+  const bool may_switch = c->inner_solver == DYSON_INNER_AUTO;
+  const MatvecFn mv = [&](const float* zero, const float* in, float* out) {
+    return matvec_f32(c, ncol, gs, precision, zero, in, out);
+  };
   for (int ref = 0; ref < c->max_refinements; ++ref) {
     float* d = nullptr;
-    rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep);
+    if (gmres) {
+      rc = gmres_inner_solve(c, ncol, r32, da, max_sweeps, kGmresTarget, rep, mv);
+      d = da;
+      rep->inner_gmres = 1;
+    } else {
+      double peak = 0.0;
+      rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep, &peak,
+                       may_switch ? kSeriesPeakMax : std::numeric_limits<double>::infinity());
+      if (rc == DYSON_ERR_DIVERGED && may_switch) {
+        gmres = true;                                    // redo this refinement with GMRES
+        --ref;
+        continue;
+      }
+    }
     if (rc == DYSON_ERR_DIVERGED) {
       status = rc;
       break;
@@ -288,9 +341,13 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
       status = DYSON_OK;
       break;
     }
-    if (res > kRefineContract * prev_res && ++strikes >= kRefineStrikes) {
-      status = DYSON_ERR_DIVERGED;
-      break;
+    if (res > kRefineContract * prev_res) {
+      if (may_switch && !gmres) {
+        gmres = true;                                    // the series does not contract: use GMRES
+      } else if (++strikes >= kRefineStrikes) {
+        status = DYSON_ERR_DIVERGED;
+        break;
+      }
     }
     prev_res = res;
   }
@@ -738,6 +795,16 @@ int dyson_set_chunk(dyson_ctx* c, int32_t block_columns) {
   return DYSON_OK;
 }
 
+int dyson_set_inner_solver(dyson_ctx* c, int solver, int32_t restart) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (solver != DYSON_INNER_SERIES && solver != DYSON_INNER_GMRES && solver != DYSON_INNER_AUTO)
+    return ctx_fail(c, DYSON_ERR_INVALID_ARG, "unknown inner solver");
+  if (restart < 0 || restart > 60) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "restart length must be 0..60");
+  c->inner_solver = solver;
+  c->gmres_restart = restart > 0 ? restart : 40;
+  return DYSON_OK;
+}
+
 int dyson_set_sweep_variant(dyson_ctx* c, int variant) {
   if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
   if (variant != DYSON_SWEEP_SINGLE_CTA && variant != DYSON_SWEEP_CTA_PAIR)
@@ -753,6 +820,7 @@ void dyson_destroy(dyson_ctx* c) {
   flush_timers(c);
   tc_release(c);
   oz_release(c);
+  gmres_release(c);
   void* ptrs[] = {c->dU, c->dJ, c->d_nbr, c->d_nbond, c->d_eps, c->d_phase, c->d_lam, c->d_JW, c->d_Jz,
                   c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_src_site, c->d_src_time,
                   c->d_norm, c->adj};

@@ -135,6 +135,9 @@ struct dyson_ctx {
   void* adj = nullptr;               // adjoint buffers (columns, rows, gathers, M, results)
   size_t adj_bytes = 0;
   void* oz = nullptr;                // split-product residual state (slices, scales, maps)
+  void* gm = nullptr;                // GMRES inner-solver state (Krylov basis, rotations)
+  int inner_solver = 2;              // DYSON_INNER_SERIES, DYSON_INNER_GMRES or DYSON_INNER_AUTO
+  int gmres_restart = 40;            // restart length (capped by free memory)
   bool oz_enabled = true;            // DYSON_NO_OZ=1 keeps the FP64 CUDA-core residual
   bool use_oz = false;               // chosen for the current solve
 

@@ -29,7 +29,8 @@ constexpr double kDivergedF64 = 4503599627370496.0;
 // Stopping rule of the FP32 inner series.  Its update first grows (the transient
 // of the real-time series), falls factorially after its peak, then settles at
 // the FP32 rounding level of the partial sums: stop at kInnerTarget, or once it
-// sits kStallDrop below its peak and has not improved for kStallSweeps sweeps.
+// sits kStallDrop below its peak and has not improved for kStallSweeps sweeps
+// (improvement counted from the latest peak, never during the growth).
 constexpr double kInnerTarget = 4e-7;
 constexpr double kStallDrop = 1e-4;
 constexpr int kStallSweeps = 4;
@@ -41,6 +42,15 @@ constexpr int kStallSweeps = 4;
 // falls, however slowly, keeps the solve going (NOT_CONVERGED at the limit).
 constexpr double kRefineContract = 1.0;
 constexpr int kRefineStrikes = 2;
+
+// An inner series whose update peaked above this (relative to the right-hand
+// side) carries FP32 rounding of about kSeriesPeakMax * 6e-8 > 1e-2 in its result,
+// too little for refinement to gain; with DYSON_INNER_AUTO the chunk continues
+// with GMRES.  Contours of the length of the 16x16 benchmark peak near 1e4.
+constexpr double kSeriesPeakMax = 1e5;
+// relative residual at which the FP32 GMRES inner solve stops (its rounding floor
+// is near 1e-6; the FP64 refinement supplies the rest)
+constexpr double kGmresTarget = 4e-6;
 
 int fail_noctx(int code, const std::string& m);           // error without a context
 double bits_to_double(unsigned long long b);

@@ -178,24 +178,83 @@ def test_slow_series_reports_not_converged(torch_cuda, lib):
 DIVERGENT = dict(L=3, Ly=3, Nt=24, Nm=16, dt=0.05, beta=2.0, trap_c=0.0, U0=4.0, J0=2.0)   # rho(K) = 1.41
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_divergent_series_reports_diverged(torch_cuda, lib, prec):
+def test_divergent_series_reports_diverged(torch_cuda, lib):
     """J/U = 1/2: the spectral radius of K is 1.41, so the series of App. C
-    diverges.  Both paths must report DIVERGED, keep the context usable and leave
-    the CUDA context clean (no launch on a missing state)."""
+    diverges.  The FP64 series and the mixed path forced to the series must
+    report DIVERGED, keep the context usable and leave the CUDA context clean
+    (no launch on a missing state)."""
     torch = torch_cuda
     from paper_1309_5994_gb300 import binding
     p = wl.small(**DIVERGENT)
     S = dyson.setup(p)
     assert np.abs(np.linalg.eigvals(dyson.dense_K(S))).max() > 1.3
     s = _solver(p)
+    s.set_inner_solver(binding.INNER_SERIES)
     g = torch.empty((1, p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda:0")
-    res = s.solve([4], precision=prec, tol=1e-12, max_sweeps=400, g_out=g, allow=(-4,))
-    assert res.status == -4
+    for prec in (0, 1):
+        res = s.solve([4], precision=prec, tol=1e-12, max_sweeps=400, g_out=g, allow=(-4,))
+        assert res.status == -4
     s.observables()                                          # the context still answers
     torch.cuda.synchronize()
     ok = _solver(wl.small(**SMALL[0]))
-    assert ok.solve([0], precision=prec, tol=1e-12).status == 0
+    assert ok.solve([0], precision=1, tol=1e-12).status == 0
+
+
+@pytest.mark.parametrize("inner", ["auto", "gmres"])
+def test_gmres_solves_where_the_series_diverges(torch_cuda, lib, inner):
+    """The same divergent problem with the GMRES inner solver of App. C (chosen by
+    AUTO after the series fails, or forced): the refined result equals the dense
+    solve to 1e-12."""
+    torch = torch_cuda
+    from paper_1309_5994_gb300 import binding
+    p = wl.random_tables(wl.small(**DIVERGENT), seed=9, rel=0.1)
+    S = dyson.setup(p)
+    s = _solver(p)
+    if inner == "gmres":
+        s.set_inner_solver(binding.INNER_GMRES, 24)
+    sources = [0, 4, 8]
+    got, res = _solve(torch, s, p, sources, 1, tol=1e-13, max_sweeps=400)
+    assert res.status == 0 and res.report["inner_gmres"] == 1
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    for q in range(len(sources)):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+
+
+@pytest.mark.parametrize("kw", [SMALL[0], TC_CASES[0], TC_CASES[1]])
+def test_forced_gmres_matches_dense(torch_cuda, lib, kw):
+    """GMRES as the inner solver on convergent problems: FP32 CUDA-core matvec
+    (Nc = 19) and the 3xTF32 tensor-core matvec (Nc = 64, 128), restart 8."""
+    torch = torch_cuda
+    from paper_1309_5994_gb300 import binding
+    p = wl.random_tables(wl.small(**kw), seed=19, rel=0.2)
+    S = dyson.setup(p)
+    s = _solver(p)
+    s.set_inner_solver(binding.INNER_GMRES, 8)
+    sources = list(range(min(p.Nr, 3)))
+    got, res = _solve(torch, s, p, sources, 1, tol=1e-13, max_sweeps=400)
+    assert res.status == 0 and res.report["inner_gmres"] == 1
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    for q in range(len(sources)):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+
+
+def test_config3_sampled_columns_mixed_gmres(torch_cuda, lib):
+    """32x32 lattice, driven, Nc = 384, one block column in mixed precision: the
+    FP32 series cannot serve here (its partial sums peak ~2e7 above the result),
+    so AUTO refines with GMRES.  Sampled vector columns against the oracle's
+    complex128 GMRES (residual 1e-12)."""
+    p = wl.config3()
+    S = dyson.setup(p)
+    s = _solver(p)
+    src = 527
+    got, res = _solve(torch_cuda, s, p, [src], 1, tol=1e-10, max_sweeps=400)
+    assert res.status == 0 and res.report["inner_gmres"] == 1
+    zs = [0, 159, 200, 330]
+    B = dyson.rhs_vector_columns(S, [(src, z) for z in zs])
+    ref, _, hist = dyson.gmres_solve(S, B, tol=1e-12, d_max=60, max_restarts=4)
+    assert hist[-1] <= 1e-12
+    for c, z in enumerate(zs):
+        assert _rel(got[0][:, :, z], ref[:, :, c]) < 1e-7
 
 
 def test_config3_sampled_columns_fp64(torch_cuda, lib):
