@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU legs (profiling runs)")
     ap.add_argument("--uneven-instances", type=int, default=64,
                     help="instances of the seeded uneven batch in the batched-solve leg (0 skips it)")
+    ap.add_argument("--no-driven", action="store_true", help="skip the driven 32x32 (Nc = 384) leg")
     ap.add_argument("--lattice", type=int, default=16,
                     help="lattice side; 16 is the benchmark workload, smaller sides serve ncu captures only")
     return ap.parse_args()
@@ -224,6 +225,45 @@ def batched_uneven_leg(args, dev, stream):
     return out
 
 
+def driven_leg(args, dev, stream):
+    """The driven 32x32 lattice (Nc = 384, U(t) = 20(1 + 0.1 sin 20t), J(t) = 1 - 0.2 sin 20t):
+    one block column near the trap centre in mixed precision (the FP32 series
+    cannot serve on this contour, so the AUTO inner solver runs GMRES) against the
+    plain FP64 series run for 105 sweeps, where its update reaches its floor."""
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_1309_5994_gb300 import binding
+    p = wl.config3()
+    s = binding.Solver(p, device=dev.index, stream=stream)
+    s.build_sigma()
+    src = [527]
+    s.solve(src, precision=binding.PREC_TF32X3_F64REF, tol=args.tol, max_sweeps=400)   # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rm = s.solve(src, precision=binding.PREC_TF32X3_F64REF, tol=args.tol, max_sweeps=400)
+    torch.cuda.synchronize(dev)
+    t_mixed = time.perf_counter() - t0
+    n_mixed = s.observables()[0][src[0]].copy()
+    t0 = time.perf_counter()
+    rf = s.solve(src, precision=binding.PREC_F64, tol=1e-15, max_sweeps=105, allow=(0, -3))
+    torch.cuda.synchronize(dev)
+    t_f64 = time.perf_counter() - t0
+    n_f64 = s.observables()[0][src[0]].copy()
+    s.close()
+    return {"workload": "32x32 driven lattice, Nc=384 (160+160 real-time points dt=0.05, 64 imaginary), "
+                        "block column of site 527",
+            "mixed": {"seconds": t_mixed, "value": 1.0 / t_mixed, "unit": UNIT, "sweeps": rm.report["sweeps"],
+                      "refinements": rm.report["refinements"], "rel_residual": rm.report["residual"],
+                      "inner_solver": "gmres" if rm.report["inner_gmres"] else "series"},
+            "plain_f64": {"seconds": t_f64, "value": 1.0 / t_f64, "unit": UNIT, "sweeps": rf.report["sweeps"],
+                          "final_update": rf.report["update"],
+                          "note": "the FP64 series' update floors near 5e-8 on this contour (partial sums peak ~2e7 "
+                                  "above the result), so it cannot reach the mixed path's residual"},
+            "speedup_vs_plain_f64": t_f64 / t_mixed,
+            "density_rel_diff_mixed_vs_f64": float(np.abs(n_mixed - n_f64).max() / np.abs(n_f64).max())}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle as the reference arm (rank 0 only)."""
     if rank != 0:
@@ -275,6 +315,9 @@ def run_gb300(args, rank, world, local):
         s.build_sigma()
         return s.solve(src, precision=PREC, tol=args.tol, max_sweeps=400)
 
+    # sweep variant and chunk picked by the library's autotuner on this workload
+    solver.build_sigma()
+    tuning = solver.autotune(args.batch)
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize(dev)
@@ -366,6 +409,8 @@ def run_gb300(args, rank, world, local):
         t0 = time.perf_counter()
         for k in range(args.steps):
             s2 = binding.Solver(p, device=local, stream=stream)
+            s2.set_sweep_variant(tuning["sweep_variant"])
+            s2.set_chunk(tuning["chunk_block_columns"])
             s2.build_sigma()
             s2.solve(dist.step_sources(p.Nr, args.batch, rank, world, k), precision=PREC, tol=args.tol,
                      max_sweeps=400)
@@ -411,6 +456,8 @@ def run_gb300(args, rank, world, local):
                 extras["cpu_baseline"] = cpu_baseline(p, args.cpu_columns)
             if args.uneven_instances > 0:
                 extras["batched_uneven"] = batched_uneven_leg(args, dev, stream)
+            if not args.no_driven:
+                extras["driven_config3"] = driven_leg(args, dev, stream)
 
     if rank != 0:
         return
@@ -427,6 +474,10 @@ def run_gb300(args, rank, world, local):
             "contour_gemm_tflops": tflops_local * world,
             "vector_columns_per_s": value * Nc,
             "sweeps_per_step": sweeps, "refinements_per_step": refinements, "max_rel_residual": residual,
+            "autotune": {"sweep_variant": ["single_cta", "cta_pair"][tuning["sweep_variant"]],
+                         "chunk_block_columns": tuning["chunk_block_columns"],
+                         "candidates": [(["single_cta", "cta_pair"][c["variant"]], c["chunk"],
+                                         round(c["vector_columns_per_s"])) for c in tuning["candidates"]]},
             "roofline": roof, "rooflines": rooflines, "kernels": kernels, "clocks": clk,
             "gpu_launches": gpu_launches}
     line.update(extras)

@@ -220,6 +220,27 @@ int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);
 enum { DYSON_SWEEP_SINGLE_CTA = 0, DYSON_SWEEP_CTA_PAIR = 1 };
 int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
 
+/* Autotuner of the tensor-core sweep.  On this context's Lambda it times two
+ * warm-up and three timed sweeps for each candidate: every sweep variant the
+ * contour allows (DYSON_SWEEP_SINGLE_CTA; DYSON_SWEEP_CTA_PAIR where Nc is a
+ * multiple of 128) times every chunk of 1, 2, 4, ... block columns up to
+ * max_block_columns and to what fits in 85 % of free device memory.  Then it
+ * sets the context to the fastest (dyson_set_sweep_variant and dyson_set_chunk)
+ * and, when out is not NULL, reports the choice and every candidate's measured
+ * sweep throughput in vector columns per second.  Needs a built, upright Lambda
+ * and Nc % 64 == 0; the work buffers keep the largest candidate's size. */
+enum { DYSON_TUNE_MAX_CANDIDATES = 32 };
+typedef struct {
+  int32_t sweep_variant;          /* chosen DYSON_SWEEP_*                                   */
+  int32_t chunk_block_columns;    /* chosen block columns per chunk                         */
+  double vector_columns_per_s;    /* measured sweep throughput of the choice                */
+  int32_t n_candidates;
+  int32_t cand_variant[DYSON_TUNE_MAX_CANDIDATES];
+  int32_t cand_chunk[DYSON_TUNE_MAX_CANDIDATES];
+  double cand_vector_columns_per_s[DYSON_TUNE_MAX_CANDIDATES];
+} dyson_tuning;
+int dyson_autotune(dyson_ctx* ctx, int32_t max_block_columns, dyson_tuning* out);
+
 /* Inner solver of the mixed-precision path (DYSON_PREC_TF32X3_F64REF), between
  * FP64 residual refinements:
  *   SERIES  the series of App. C in FP32;
@@ -247,7 +268,9 @@ int dyson_set_inner_solver(dyson_ctx* ctx, int solver, int32_t restart);
  * launch over the tiles of all instances still iterating, followed by a check
  * kernel that applies each instance's stopping rule on the device.  Blocks of
  * graph_sweeps sweeps are captured once as a CUDA graph and replayed with no
- * host round trip inside a block.
+ * host round trip inside a block.  An instance whose series diverges (spectral
+ * radius of Lambda W J above 1) is afterwards solved alone with the GMRES inner
+ * solver of App. C, unless its context was set to DYSON_INNER_SERIES.
  *
  * Requirements: every context is on the same device and stream, its Lambda is
  * built and upright, and its contour suits the tensor-core path with the

@@ -42,6 +42,20 @@ class Drive(C.Structure):
     _fields_ = [("U", C.POINTER(C.c_double)), ("J", C.POINTER(C.c_double))]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("sweep_variant", C.c_int32), ("chunk_block_columns", C.c_int32),
+                ("vector_columns_per_s", C.c_double), ("n_candidates", C.c_int32),
+                ("cand_variant", C.c_int32 * 32), ("cand_chunk", C.c_int32 * 32),
+                ("cand_vector_columns_per_s", C.c_double * 32)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {"sweep_variant": self.sweep_variant, "chunk_block_columns": self.chunk_block_columns,
+                "vector_columns_per_s": self.vector_columns_per_s,
+                "candidates": [{"variant": self.cand_variant[k], "chunk": self.cand_chunk[k],
+                                "vector_columns_per_s": self.cand_vector_columns_per_s[k]} for k in range(n)]}
+
+
 class Report(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("refinements", C.c_int32), ("chunks", C.c_int32),
                 ("status", C.c_int32), ("update", C.c_double), ("residual", C.c_double),
@@ -58,7 +72,7 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
-           "dyson_batch_destroy", "dyson_set_inner_solver"]
+           "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune"]
 INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
 
@@ -88,6 +102,7 @@ def load(path: str = _LIB_PATH):
     lib.dyson_set_chunk.argtypes = [P, C.c_int32]
     lib.dyson_set_sweep_variant.argtypes = [P, C.c_int]
     lib.dyson_set_inner_solver.argtypes = [P, C.c_int, C.c_int32]
+    lib.dyson_autotune.argtypes = [P, C.c_int32, C.POINTER(Tuning)]
     lib.dyson_launch_count.argtypes = [P]
     lib.dyson_launch_count.restype = C.c_int64
     lib.dyson_solve_block_column_noalloc.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
@@ -232,6 +247,12 @@ class Solver:
 
     def set_chunk(self, cols: int):
         self._check(self.lib.dyson_set_chunk(self.h, cols))
+
+    def autotune(self, max_block_columns: int) -> dict:
+        """Time the sweep candidates on this context, keep the fastest; returns the report."""
+        t = Tuning()
+        self._check(self.lib.dyson_autotune(self.h, max_block_columns, C.byref(t)))
+        return t.as_dict()
 
     def set_inner_solver(self, solver: int, restart: int = 0):
         self._check(self.lib.dyson_set_inner_solver(self.h, solver, restart))

@@ -11,7 +11,9 @@
 // graph_sweeps sweeps is captured once as a CUDA graph and replayed until no
 // instance is active, so the host reads one word per replay instead of
 // synchronising after every sweep.  The FP64 residual refinement (split-product
-// residual, k_oz.cu) runs per instance between inner solves.
+// residual, k_oz.cu) runs per instance between inner solves.  An instance whose
+// series diverges (spectral radius of K above 1) is then solved alone with the
+// GMRES of App. C (k_gmres.cu).
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -64,7 +66,9 @@ __global__ void k_batch_check(const BatchCheck* __restrict__ chk, int n, int* __
     S.sweeps += 1;
     S.last = upd;
     bool stop = false;
-    if (bad || !(upd < kDivergedGrowth)) {
+    if (bad || !(upd < kDivergedGrowth) || upd > kSeriesPeakMax) {
+      // not finite, or a transient the FP32 series cannot carry: hand the
+      // instance to the GMRES of App. C after the batch
       S.diverged = 1;
       stop = true;
     } else {
@@ -408,6 +412,21 @@ int dyson_batch_solve(dyson_batch* b, const int32_t* const* src, const int32_t* 
       }
       X.prev_res = res;
     }
+  }
+  // ---- instances whose series diverged: the GMRES of App. C, one context at a
+  //      time (unless the context asked for the series alone) ----
+  for (int k = 0; k < n; ++k) {
+    Inst& X = I[k];
+    dyson_ctx* c = X.c;
+    if (X.status != DYSON_ERR_DIVERGED || c->inner_solver == DYSON_INNER_SERIES) continue;
+    const int saved = c->inner_solver;
+    c->inner_solver = DYSON_INNER_GMRES;
+    double2* G = nullptr;
+    rc = solve_mixed(c, X.ncol, c->Nc, DYSON_PREC_TF32X3_F64REF, tol, max_sweeps, &G, &X.rep);
+    c->inner_solver = saved;
+    if (rc != DYSON_OK && rc != DYSON_ERR_NOT_CONVERGED && rc != DYSON_ERR_DIVERGED) return bfail(b, rc, c->err);
+    X.status = rc;
+    X.G = G;
   }
   // ---- observables and optional export per instance ----
   int status = DYSON_OK;

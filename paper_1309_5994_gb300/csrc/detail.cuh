@@ -63,6 +63,9 @@ double rel_max(const unsigned long long* norm, const double* ref, int ng);
 double sweep_flops(const dyson_ctx* c, int ncol);         // algorithmic contour-GEMM flops of one sweep
 // reduced-precision copies of Lambda; sets c->use_tc, c->use_oz
 int prepare_tables(dyson_ctx* c, int precision);
+// mixed-precision solve of the chunk whose sources are on the device (G in c->work)
+int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int max_sweeps, double2** result,
+                dyson_report* rep);
 // vector columns per chunk that fit in device memory (multiple of unit, at most want)
 int64_t chunk_columns(dyson_ctx* c, int precision, int64_t unit, int64_t want, size_t* bytes_per_col);
 

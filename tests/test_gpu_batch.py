@@ -141,21 +141,28 @@ def test_uneven_batch_config4_sampled(torch_cuda, lib):
     b.close()
 
 
-def test_batch_reports_a_divergent_member_and_solves_the_rest(torch_cuda, lib):
-    """One instance with rho(K) = 1.41 (J/U = 1/2) among convergent ones: the batch
-    returns DIVERGED for it and still solves the others to 1e-12."""
+@pytest.mark.parametrize("inner", ["series", "auto"])
+def test_batch_with_a_divergent_member(torch_cuda, lib, inner):
+    """One instance with rho(K) = 1.41 (J/U = 1/2) among convergent ones.  With the
+    series only, the batch returns DIVERGED for it and still solves the others to
+    1e-12; by default the divergent member is then solved by GMRES, to 1e-12 too."""
     torch = torch_cuda
     from paper_1309_5994_gb300 import binding
     divergent = wl.small(L=3, Ly=3, Nt=24, Nm=16, dt=0.05, beta=2.0, trap_c=0.0, U0=4.0, J0=2.0)
     problems = [wl.random_tables(wl.small(**SMALL[0]), seed=41, rel=0.2), divergent,
                 wl.random_tables(wl.small(**SMALL[1]), seed=42, rel=0.2)]
     solvers, _ = _solvers(torch, problems)
+    if inner == "series":
+        solvers[1].set_inner_solver(binding.INNER_SERIES)
     sources = [[1], [4], [2]]
     g = [torch.empty((1, p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda:0") for p in problems]
     b = binding.Batch(solvers)
-    res = b.solve(sources, tol=1e-12, g_outs=g, allow=(-4,))
-    assert [r.status for r in res] == [0, -4, 0]
-    for k in (0, 2):
+    res = b.solve(sources, tol=1e-12, g_outs=g, allow=(0, -4))
+    if inner == "series":
+        assert [r.status for r in res] == [0, -4, 0]
+    else:
+        assert [r.status for r in res] == [0, 0, 0] and res[1].report["inner_gmres"] == 1
+    for k in ((0, 2) if inner == "series" else (0, 1, 2)):
         p = problems[k]
         S = dyson.setup(p)
         ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources[k]))

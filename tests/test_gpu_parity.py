@@ -122,6 +122,27 @@ def test_pair_kernel_ragged_column_tiles(torch_cuda, lib):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
 
+def test_autotune_picks_a_measured_candidate_and_solves(torch_cuda, lib):
+    """Nc = 128: the tuner times both sweep variants over chunks of 1, 2, 4, 6 block
+    columns, keeps the fastest, and the solve under that choice still equals the
+    dense solve."""
+    p = wl.random_tables(wl.small(**TC_CASES[1]), seed=23, rel=0.2)
+    S = dyson.setup(p)
+    s = _solver(p)
+    t = s.autotune(6)
+    cands = t["candidates"]
+    assert {c["chunk"] for c in cands} == {1, 2, 4, 6} and {c["variant"] for c in cands} == {0, 1}
+    best = max(cands, key=lambda c: c["vector_columns_per_s"])
+    assert (t["sweep_variant"], t["chunk_block_columns"]) == (best["variant"], best["chunk"])
+    assert all(c["vector_columns_per_s"] > 0 for c in cands)
+    sources = list(range(p.Nr))
+    got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
+    assert res.report["chunks"] == -(-len(sources) // t["chunk_block_columns"])
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    for q in range(len(sources)):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_config1_all_columns_and_observables(torch_cuda, lib, prec):
     p = wl.config1()
