@@ -264,6 +264,35 @@ def driven_leg(args, dev, stream):
             "density_rel_diff_mixed_vs_f64": float(np.abs(n_mixed - n_f64).max() / np.abs(n_f64).max())}
 
 
+def wedge_leg(args, dev, stream, tuning):
+    """All 256 sources of the 16x16 workload, whose centred trap and uniform drive
+    keep C4v (App. A): the 36 orbit representatives are solved and the other
+    sites' observables filled by symmetry."""
+    import torch
+    import workloads as wl
+    from paper_1309_5994_gb300 import binding
+    p = wl.config2()
+    s = binding.Solver(p, device=dev.index, stream=stream)
+    s.set_sweep_variant(tuning["sweep_variant"])
+    s.set_chunk(tuning["chunk_block_columns"])
+    s.build_sigma()
+    s.set_symmetry(binding.SYMMETRY_C4V)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r = s.solve(list(range(p.Nr)), precision=binding.PREC_TF32X3_F64REF, tol=args.tol, max_sweeps=400)
+    n, _, _ = s.observables()
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    s.close()
+    L = p.Lx
+    orbits = {min(y2 * L + x2 for x2, y2 in ((x, y), (L - 1 - x, y), (x, L - 1 - y), (y, x), (L - 1 - y, L - 1 - x),
+                                              (L - 1 - x, L - 1 - y), (y, L - 1 - x), (L - 1 - y, x)))
+              for y in range(L) for x in range(L)}
+    return {"sources": p.Nr, "representatives_solved": len(orbits), "status": r.status,
+            "seconds": dt, "site_observables_per_s": p.Nr / dt, "unit": "sources with observables per second",
+            "note": "not the benchmark metric: block columns actually solved are the orbit representatives"}
+
+
 def run_reference(args, rank, world):
     """The CPU oracle as the reference arm (rank 0 only)."""
     if rank != 0:
@@ -458,6 +487,7 @@ def run_gb300(args, rank, world, local):
                 extras["batched_uneven"] = batched_uneven_leg(args, dev, stream)
             if not args.no_driven:
                 extras["driven_config3"] = driven_leg(args, dev, stream)
+            extras["c4v_wedge_all_sources"] = wedge_leg(args, dev, stream, tuning)
 
     if rank != 0:
         return

@@ -220,6 +220,18 @@ int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);
 enum { DYSON_SWEEP_SINGLE_CTA = 0, DYSON_SWEEP_CTA_PAIR = 1 };
 int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
 
+/* Point-group symmetry of the problem (App. A).  DYSON_SYMMETRY_C4V: on a
+ * square lattice with the centred trap and drive tables invariant under the
+ * eight operations of C4v (checked exactly here; INVALID_ARG otherwise),
+ * dyson_solve_columns solves one source per symmetry orbit, the smallest site
+ * index of the orbit, about Nr/8 block columns for all sources.  It fills the
+ * other sources' observables by copies, and their G, when g_out is given, by
+ * the site permutation G_{j,s} = G_{g^-1(j),r} for s = g(r).  The report
+ * counts the solved representatives only.  DYSON_SYMMETRY_NONE (the default)
+ * solves every source. */
+enum { DYSON_SYMMETRY_NONE = 0, DYSON_SYMMETRY_C4V = 1 };
+int dyson_set_symmetry(dyson_ctx* ctx, int mode);
+
 /* Autotuner of the tensor-core sweep.  On this context's Lambda it times two
  * warm-up and three timed sweeps for each candidate: every sweep variant the
  * contour allows (DYSON_SWEEP_SINGLE_CTA; DYSON_SWEEP_CTA_PAIR where Nc is a

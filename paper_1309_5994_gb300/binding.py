@@ -72,7 +72,8 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
-           "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune"]
+           "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune", "dyson_set_symmetry"]
+SYMMETRY_NONE, SYMMETRY_C4V = 0, 1
 INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
 
@@ -103,6 +104,7 @@ def load(path: str = _LIB_PATH):
     lib.dyson_set_sweep_variant.argtypes = [P, C.c_int]
     lib.dyson_set_inner_solver.argtypes = [P, C.c_int, C.c_int32]
     lib.dyson_autotune.argtypes = [P, C.c_int32, C.POINTER(Tuning)]
+    lib.dyson_set_symmetry.argtypes = [P, C.c_int]
     lib.dyson_launch_count.argtypes = [P]
     lib.dyson_launch_count.restype = C.c_int64
     lib.dyson_solve_block_column_noalloc.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
@@ -247,6 +249,9 @@ class Solver:
 
     def set_chunk(self, cols: int):
         self._check(self.lib.dyson_set_chunk(self.h, cols))
+
+    def set_symmetry(self, mode: int):
+        self._check(self.lib.dyson_set_symmetry(self.h, mode))
 
     def autotune(self, max_block_columns: int) -> dict:
         """Time the sweep candidates on this context, keep the fastest; returns the report."""

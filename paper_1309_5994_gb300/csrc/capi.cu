@@ -10,6 +10,7 @@
 #include "detail.cuh"
 #include "gmres.cuh"
 #include "oz.cuh"
+#include "symmetry.cuh"
 #include "tc.cuh"
 
 namespace dyson_detail {
@@ -429,6 +430,8 @@ int dyson_init(dyson_ctx** out, const dyson_lattice* L, const dyson_contour* C, 
       if (y + 1 < c->Ly) { nbr[i * 4 + 2] = i + c->Lx; nbond[i * 4 + 2] = vb + y * c->Lx + x; }
       if (y > 0) { nbr[i * 4 + 3] = i - c->Lx; nbond[i * 4 + 3] = vb + (y - 1) * c->Lx + x; }
     }
+  c->h_nbr = nbr;
+  c->h_nbond = nbond;
   const size_t NcNc = (size_t)c->Nc * c->Nc;
   auto bail = [&](cudaError_t e, const char* what) {
     int code = e == cudaErrorMemoryAllocation ? DYSON_ERR_OOM : DYSON_ERR_CUDA;
@@ -578,6 +581,8 @@ extern "C" {
 int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
                         int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
   if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (c->symmetry == DYSON_SYMMETRY_C4V)
+    return solve_columns_c4v(c, src, n_src, precision, tol, max_sweeps, g_out, rep_out);
   ReportScope R(c, rep_out);
   int rc = check_solve_args(c, precision, tol, max_sweeps);
   if (rc) return R.finish(rc);
@@ -821,6 +826,7 @@ void dyson_destroy(dyson_ctx* c) {
   tc_release(c);
   oz_release(c);
   gmres_release(c);
+  if (c->d_sym_perm) cudaFree(c->d_sym_perm);
   void* ptrs[] = {c->dU, c->dJ, c->d_nbr, c->d_nbond, c->d_eps, c->d_phase, c->d_lam, c->d_JW, c->d_Jz,
                   c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_src_site, c->d_src_time,
                   c->d_norm, c->adj};

@@ -136,6 +136,10 @@ struct dyson_ctx {
   size_t adj_bytes = 0;
   void* oz = nullptr;                // split-product residual state (slices, scales, maps)
   void* gm = nullptr;                // GMRES inner-solver state (Krylov basis, rotations)
+  std::vector<int> h_nbr, h_nbond;   // host copies of the neighbour tables
+  int symmetry = 0;                  // DYSON_SYMMETRY_NONE or DYSON_SYMMETRY_C4V
+  std::vector<int> sym_rep, sym_op;  // per site: orbit representative, an operation taking it there
+  int* d_sym_perm = nullptr;         // [8][Nr]: site j <- g^{-1}(j) for each operation g
   int inner_solver = 2;              // DYSON_INNER_SERIES, DYSON_INNER_GMRES or DYSON_INNER_AUTO
   int gmres_restart = 40;            // restart length (capped by free memory)
   bool oz_enabled = true;            // DYSON_NO_OZ=1 keeps the FP64 CUDA-core residual

@@ -122,6 +122,36 @@ def test_pair_kernel_ragged_column_tiles(torch_cuda, lib):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
 
+def test_c4v_wedge_solve_equals_the_full_solve(torch_cuda, lib):
+    """App. A: a centred trap and a uniform drive keep C4v.  The 4x4 lattice has 3
+    orbits (corners, edges, centre); solving their representatives and filling the
+    rest by symmetry gives every block column and observable of the full solve."""
+    torch = torch_cuda
+    from paper_1309_5994_gb300 import binding
+    p = wl.small(L=4, Ly=4, Nt=24, Nm=16, trap_c=0.3, U0=20.0, aU=0.1, aJ=0.2, omega=20.0)
+    S = dyson.setup(p)
+    sources = list(range(p.Nr))
+    full = _solver(p)
+    g_full, r_full = _solve(torch, full, p, sources, 1, tol=1e-13)
+    n_full, e_full, d_full = full.observables()
+    sym = _solver(p)
+    sym.set_symmetry(binding.SYMMETRY_C4V)
+    g_sym, r_sym = _solve(torch, sym, p, sources, 1, tol=1e-13)
+    n_sym, e_sym, d_sym = sym.observables()
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    for q in range(p.Nr):
+        assert _rel(g_sym[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+        assert _rel(g_sym[q], g_full[q]) < 1e-12
+    assert np.abs(n_sym - n_full).max() < 1e-12 and np.abs(e_sym - e_full).max() < 1e-12
+    assert np.allclose(d_sym[:, 1:], d_full[:, 1:], rtol=0, atol=1e-10)
+    # three representatives solved instead of sixteen block columns
+    assert r_sym.report["gemm_flops"] < 0.3 * r_full.report["gemm_flops"]
+    bad = _solver(wl.random_tables(p, seed=2, rel=0.1))
+    with pytest.raises(binding.DysonError) as e:
+        bad.set_symmetry(binding.SYMMETRY_C4V)
+    assert e.value.code == -1
+
+
 def test_autotune_picks_a_measured_candidate_and_solves(torch_cuda, lib):
     """Nc = 128: the tuner times both sweep variants over chunks of 1, 2, 4, 6 block
     columns, keeps the fastest, and the solve under that choice still equals the
