@@ -102,29 +102,33 @@ __global__ void __launch_bounds__(GM_THREADS) k_gm_dots(const float* __restrict_
   const int s0 = blockIdx.z * sites_per_blk, s1 = min(Nr, s0 + sites_per_blk);
   const float* __restrict__ q = Q + (size_t)i * vsz;
   const bool self = nrm0 && i == 0;
-  // The block's (site, element) range is walked four elements per thread at a
-  // time (independent loads in flight); FP32 products are summed in FP32 over
-  // those four and in FP64 beyond - GB300's FP64 pipe is too slow for a product
-  // per element.
-  const int total = (s1 - s0) * Nc;
+  // Each warp walks the block's sites (stride: warps per block), its lanes the
+  // contour index, four elements per lane at a time (independent loads in
+  // flight).  FP32 products are summed in FP32 within a site and in FP64 across
+  // sites - GB300's FP64 pipe is too slow for a product per element.
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   double re = 0.0, im = 0.0, sq = 0.0;
-  for (int e0 = threadIdx.x; e0 < total; e0 += 4 * blockDim.x) {
+  for (int s = s0 + warp; s < s1; s += nwarps) {
+    const size_t base = ((size_t)s * ncol + n) * 2 * Nc;
+    const float* __restrict__ ar = a + base;
+    const float* __restrict__ br = b ? b + base : nullptr;
+    const float* __restrict__ qr_ = q + base;
     float sre = 0.f, sim = 0.f, ssq = 0.f;
+    for (int z0 = lane; z0 < Nc; z0 += 128) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int e = e0 + k * blockDim.x;
-      if (e < total) {
-        const int ds = e / Nc, z = e - ds * Nc;
-        const size_t base = ((size_t)(s0 + ds) * ncol + n) * 2 * Nc;
-        float wr = a[base + z], wi = a[base + Nc + z];
-        if (b) {
-          wr -= b[base + z];
-          wi -= b[base + Nc + z];
+      for (int k = 0; k < 4; ++k) {
+        const int z = z0 + 32 * k;
+        if (z < Nc) {
+          float wr = ar[z], wi = ar[Nc + z];
+          if (br) {
+            wr -= br[z];
+            wi -= br[Nc + z];
+          }
+          const float qre = qr_[z], qim = qr_[Nc + z];
+          sre = fmaf(qre, wr, fmaf(qim, wi, sre));    // conj(q) w
+          sim = fmaf(qre, wi, fmaf(-qim, wr, sim));
+          if (self) ssq = fmaf(wr, wr, fmaf(wi, wi, ssq));
         }
-        const float qr = q[base + z], qi = q[base + Nc + z];
-        sre = fmaf(qr, wr, fmaf(qi, wi, sre));    // conj(q) w
-        sim = fmaf(qr, wi, fmaf(-qi, wr, sim));
-        if (self) ssq = fmaf(wr, wr, fmaf(wi, wi, ssq));
       }
     }
     re += sre;
