@@ -1,4 +1,5 @@
-"""Gradients of a weighted density sum (no counterpart in the paper; derived here).
+"""Gradients of weighted sums of site densities and double occupancies (no
+counterpart in the paper; derived here).
 
 Loss:   L = sum_i w_i n_i(t_f),  n_i(t_f) = Re[-i G_ii(z_f, z_f)],  z_f = forward point t_f.
 
@@ -126,4 +127,128 @@ def gradients(p, w, solver="dense"):
         for k in range(Nt):
             dLam = atomic_gf_dU(c, S.eps[l], S.U[l], c.beta, k)
             gU[l, k] = np.real(-1j * np.sum(dLam * M.T))
+    return L, gU, gJ
+
+
+# ----------------------------------------------------------------------------
+# densities and double occupancies: L = sum_i w_i n_i(t_f) + v_i D_i(t_f)
+# ----------------------------------------------------------------------------
+#
+# Both observables of Sec. III.A / Eq. (docc) at the forward time t_f are
+# real-linear in the column c_i = G e_(i, z_f) (z_f the forward point of t_f):
+#   n_i = Im c_i(i, z_f),
+#   D_i = [ (Re c_i(i, z_f) - Re c_i(i, z_f - 1)) / dt - eps_i n_i
+#           - Im sum_j J_ij(t_f) c_i(j, z_f) ] / U_i(t_f),
+# so L = sum_i Re(beta_i . c_i) with a sparse complex weight vector beta_i, and
+#   dL = sum_i Re(beta_i . dG e_i) + (explicit terms of D)
+# with beta_i . dG e_i = rho_i^T dLambda gamma_i + psi_i^T W dJ c_i, where
+# psi_i = sum_a beta_ia r_a (rows of G at the entries a of beta_i),
+# rho_i = beta_i + W J psi_i and gamma_i = e_i + W J c_i.  The explicit terms:
+# dD_i/dU_i(t_f) = -D_i / U_i(t_f); through eps_i = V - U_i(0)/2 - mu,
+# dD_i/dU_i(0) = n_i / (2 U_i(t_f)); through e_kin,
+# dD_i/dJ_ij(t_f) = -Im c_i(j, z_f) / U_i(t_f).
+
+def _obs_weights(S: Setup, w, v, kf):
+    """beta_i as {(site, point): coefficient} for every i."""
+    dt, zf = S.contour.dt, kf
+    out = []
+    for i in range(S.Nr):
+        b = {}
+        def add(key, val):
+            b[key] = b.get(key, 0.0) + val
+        if w is not None and w[i] != 0.0:
+            add((i, zf), -1j * w[i])                            # Im x = Re(-i x)
+        if v is not None and v[i] != 0.0:
+            Ui = S.U[i, kf]
+            add((i, zf), v[i] / (dt * Ui))
+            add((i, zf - 1), -v[i] / (dt * Ui))
+            add((i, zf), v[i] * 1j * S.eps[i] / Ui)             # -eps Im x = Re(i eps x)
+            for j, bnd in S.nbrs[i]:
+                add((j, zf), v[i] * 1j * S.Jz[bnd][zf] / Ui)     # -J Im x = Re(i J x)
+        out.append(b)
+    return out
+
+
+def obs_loss(p, w=None, v=None, t_index=None) -> float:
+    """L = sum_i w_i n_i(t_f) + v_i D_i(t_f) from the dense forward solve (t_f >= 1)."""
+    S = setup(p)
+    kf = p.Nt - 1 if t_index is None else t_index
+    C = dense_solve(S, rhs_vector_columns(S, [(i, kf) for i in range(S.Nr)]))
+    dt = S.contour.dt
+    L = 0.0
+    for i in range(S.Nr):
+        c = C[:, :, i]
+        n = np.imag(c[i, kf])
+        if w is not None:
+            L += w[i] * n
+        if v is not None:
+            ekin = np.imag(sum(S.Jz[b][kf] * c[j, kf] for j, b in S.nbrs[i]))
+            D = ((np.real(c[i, kf]) - np.real(c[i, kf - 1])) / dt - S.eps[i] * n - ekin) / S.U[i, kf]
+            L += v[i] * D
+    return float(L)
+
+
+def obs_gradients(p, w=None, v=None, t_index=None):
+    """(L, dL/dU [Nr, Nt], dL/dJ [Nb, Nt]) of L = sum_i w_i n_i(t_f) + v_i D_i(t_f)."""
+    S = setup(p)
+    c = S.contour
+    Nr, Nc, Nt = S.Nr, S.Nc, c.Nt
+    kf = Nt - 1 if t_index is None else t_index
+    assert 1 <= kf < Nt
+    betas = _obs_weights(S, w, v, kf)
+    C = dense_solve(S, rhs_vector_columns(S, [(i, kf) for i in range(Nr)]))
+    ST = transposed_setup(S)
+    keys = sorted({key for b in betas for key in b})
+    Rk = dense_solve(ST, rhs_vector_columns(ST, keys))             # rows of G at the weighted entries
+    col = {key: n for n, key in enumerate(keys)}
+    Psi = np.zeros((Nr, Nc, Nr), dtype=np.complex128)
+    for i, b in enumerate(betas):
+        for key, val in b.items():
+            Psi[:, :, i] += val * Rk[:, :, col[key]]
+    L = float(sum(np.real(sum(val * C[a, z, i] for (a, z), val in b.items())) for i, b in enumerate(betas)))
+    W = c.W
+    Zk = [[z for z in range(Nc) if (c.branch[z] != IMAG and c.k[z] == k) or (k == 0 and c.branch[z] == IMAG)]
+          for k in range(Nt)]
+    from .lattice import bond_list
+    bonds = bond_list(S.Lx, S.Ly)
+    gJ = np.zeros((len(bonds), Nt))
+    for bnd, (l, m) in enumerate(bonds):
+        for k in range(Nt):
+            z = np.array(Zk[k])
+            val = np.sum(W[z][:, None] * (Psi[l, z, :] * C[m, z, :] + Psi[m, z, :] * C[l, z, :]))
+            gJ[bnd, k] = np.real(val)
+    gU = np.zeros((Nr, Nt))
+    for l in range(Nr):
+        gam = np.zeros((Nc, Nr), dtype=np.complex128)
+        rho = np.zeros((Nc, Nr), dtype=np.complex128)
+        for m_, bnd in S.nbrs[l]:
+            gam += (W * S.Jz[bnd])[:, None] * C[m_]
+            rho += (W * S.Jz[bnd])[:, None] * Psi[m_]
+        gam[kf, l] += 1.0
+        for i, b in enumerate(betas):
+            for (a, z), val in b.items():
+                if a == l:
+                    rho[z, i] += val
+        M = gam @ rho.T                                              # M_l = sum_i gamma_i rho_i^T
+        for k in range(Nt):
+            dLam = atomic_gf_dU(c, S.eps[l], S.U[l], c.beta, k)
+            gU[l, k] = np.real(np.sum(dLam * M.T))
+    # explicit dependence of D on U(t_f), U(0) (through eps) and J(t_f)
+    if v is not None:
+        dt = c.dt
+        bond_of = {}
+        for bnd, (l, m) in enumerate(bonds):
+            bond_of[(l, m)] = bond_of[(m, l)] = bnd
+        for i in range(Nr):
+            if v[i] == 0.0:
+                continue
+            ci = C[:, :, i]
+            n = np.imag(ci[i, kf])
+            ekin = np.imag(sum(S.Jz[b][kf] * ci[j, kf] for j, b in S.nbrs[i]))
+            Ui = S.U[i, kf]
+            D = ((np.real(ci[i, kf]) - np.real(ci[i, kf - 1])) / dt - S.eps[i] * n - ekin) / Ui
+            gU[i, kf] += v[i] * (-D / Ui)
+            gU[i, 0] += v[i] * n / (2.0 * Ui)
+            for j, b in S.nbrs[i]:
+                gJ[b, kf] += v[i] * (-np.imag(ci[j, kf]) / Ui)
     return L, gU, gJ

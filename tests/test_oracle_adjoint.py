@@ -62,3 +62,32 @@ def test_amplitude_gradient_is_the_chain_rule():
     h = 1e-4
     fd = (adjoint.loss(make(1.0 + h), w) - adjoint.loss(make(1.0 - h), w)) / (2 * h)
     assert abs(fd - chain) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_density_and_double_occupancy_gradients_match_finite_differences():
+    """L = sum_i w_i n_i(t_f) + v_i D_i(t_f): the generalised adjoint (rows of G at
+    the entries D reads, plus D's explicit dependence on U(t_f), U(0) and J(t_f))
+    against central differences of the forward observables; with v = 0 it is the
+    density adjoint exactly."""
+    p = _problem()
+    rng = np.random.default_rng(2)
+    w, v = rng.uniform(0, 1, p.Nr), rng.uniform(0, 1, p.Nr)
+    L0, gU0, gJ0 = adjoint.gradients(p, w)
+    L1, gU1, gJ1 = adjoint.obs_gradients(p, w=w)
+    assert abs(L0 - L1) < 1e-14 and np.abs(gU0 - gU1).max() < 1e-15 and np.abs(gJ0 - gJ1).max() < 1e-15
+    kf = 3
+    L, gU, gJ = adjoint.obs_gradients(p, w=w, v=v, t_index=kf)
+    assert abs(L - adjoint.obs_loss(p, w, v, kf)) < 1e-13
+    h = 1e-5
+    for (l, k) in [(0, 0), (2, 1), (4, kf), (1, kf), (5, 4)]:
+        Up, Um = p.U.copy(), p.U.copy()
+        Up[l, k] += h
+        Um[l, k] -= h
+        fd = (adjoint.obs_loss(p.with_tables(U=Up), w, v, kf) - adjoint.obs_loss(p.with_tables(U=Um), w, v, kf)) / (2 * h)
+        assert abs(fd - gU[l, k]) < 1e-7 * max(1.0, abs(fd)), (l, k, fd, gU[l, k])
+    for (b, k) in [(0, 0), (3, 2), (6, kf), (2, kf)]:
+        Jp, Jm = p.J.copy(), p.J.copy()
+        Jp[b, k] += h
+        Jm[b, k] -= h
+        fd = (adjoint.obs_loss(p.with_tables(J=Jp), w, v, kf) - adjoint.obs_loss(p.with_tables(J=Jm), w, v, kf)) / (2 * h)
+        assert abs(fd - gJ[b, k]) < 1e-7 * max(1.0, abs(fd)), (b, k, fd, gJ[b, k])
