@@ -172,6 +172,19 @@ int dyson_transpose_sigma(dyson_ctx* ctx);
 int dyson_adjoint(dyson_ctx* ctx, const double* w, int32_t t_index, int precision, double tol,
                   int32_t max_sweeps, double* loss, double* grad_U, double* grad_J, dyson_report* rep);
 
+/* The same adjoint for L = sum_i w_density[i] n_i(t_f) + w_docc[i] D_i(t_f), the
+ * double occupancy D of Eq. (docc) read as dyson_observables reads it (App. B's
+ * one-sided difference; t_index >= 1).  Either weight array may be NULL, not both.
+ * D is real-linear in the same column G e_(i, t_f), through its entries at
+ * (i, t_f), (i, t_f - 1) and the neighbours (j, t_f), so the gradient needs the
+ * rows of G at (i, t_f) and (i, t_f - 1): 2 Nr transposed vector-column solves
+ * besides the Nr columns.  It also takes D's explicit dependence on U_i(t_f)
+ * (1/U), U_i(0) (through eps_i) and J_ij(t_f) (through e_kin).  Layouts and
+ * codes as dyson_adjoint. */
+int dyson_adjoint_obs(dyson_ctx* ctx, const double* w_density, const double* w_docc, int32_t t_index,
+                      int precision, double tol, int32_t max_sweeps, double* loss, double* grad_U, double* grad_J,
+                      dyson_report* rep);
+
 /* Observables of the sites solved so far (Sec. III.A, Eq. (docc), App. B):
  * density per spin n_i(t_k), kinetic energy ekin_i(t_k) and double occupancy
  * D_i(t_k), each [Nr][Nt] doubles.  Sites never solved hold NaN; D_i(t_0) is

@@ -1,6 +1,6 @@
-"""torch.autograd bridge to dyson_adjoint: differentiable weighted site densities.
+"""torch.autograd bridge to the adjoint: differentiable weighted site observables.
 
-    L = sum_i w_i n_i(t_k)
+    L = sum_i w_i n_i(t_k) + v_i D_i(t_k)      (densities and double occupancies)
 
 as a function of the drive tables U [Nr, Nt] and J [Nb, Nt] (float64 torch
 tensors).  The forward pass calls the C ABI's dyson_adjoint (forward columns,
@@ -18,14 +18,13 @@ import torch
 from . import binding
 
 
-class WeightedDensity(torch.autograd.Function):
+class WeightedObservables(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, U, J, problem, w, t_index, precision, tol):
+    def forward(ctx, U, J, problem, w, v, t_index, precision, tol):
         p = problem.with_tables(U=U.detach().cpu().numpy(), J=J.detach().cpu().numpy())
         solver = binding.Solver(p, device=torch.cuda.current_device())
         solver.build_sigma()
-        loss, gU, gJ, _ = solver.adjoint(np.asarray(w, dtype=np.float64), t_index=t_index, precision=precision,
-                                         tol=tol)
+        loss, gU, gJ, _ = solver.adjoint_obs(w, v, t_index=t_index, precision=precision, tol=tol)
         solver.close()
         ctx.save_for_backward(torch.from_numpy(gU).to(U), torch.from_numpy(gJ).to(J))
         return torch.tensor(loss, dtype=torch.float64, device=U.device)
@@ -33,10 +32,16 @@ class WeightedDensity(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         gU, gJ = ctx.saved_tensors
-        return grad_out * gU, grad_out * gJ, None, None, None, None, None
+        return grad_out * gU, grad_out * gJ, None, None, None, None, None, None
+
+
+def weighted_observables(U, J, problem, w=None, v=None, t_index=None, precision=binding.PREC_TF32X3_F64REF,
+                         tol=1e-11):
+    """Differentiable L = sum_i w_i n_i(t_index) + v_i D_i(t_index) (default: the last forward time)."""
+    t_index = problem.Nt - 1 if t_index is None else t_index
+    return WeightedObservables.apply(U, J, problem, w, v, t_index, precision, tol)
 
 
 def weighted_density(U, J, problem, w, t_index=None, precision=binding.PREC_TF32X3_F64REF, tol=1e-11):
     """Differentiable L = sum_i w_i n_i(t_index) (default: the last forward time)."""
-    t_index = problem.Nt - 1 if t_index is None else t_index
-    return WeightedDensity.apply(U, J, problem, w, t_index, precision, tol)
+    return weighted_observables(U, J, problem, w=w, t_index=t_index, precision=precision, tol=tol)

@@ -72,7 +72,8 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
-           "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune", "dyson_set_symmetry"]
+           "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune", "dyson_set_symmetry",
+           "dyson_adjoint_obs"]
 SYMMETRY_NONE, SYMMETRY_C4V = 0, 1
 INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
@@ -98,6 +99,8 @@ def load(path: str = _LIB_PATH):
                                                C.c_double, C.c_int32, P, C.POINTER(Report)]
     lib.dyson_transpose_sigma.argtypes = [P]
     lib.dyson_adjoint.argtypes = [P, P, C.c_int32, C.c_int, C.c_double, C.c_int32, P, P, P, C.POINTER(Report)]
+    lib.dyson_adjoint_obs.argtypes = [P, P, P, C.c_int32, C.c_int, C.c_double, C.c_int32, P, P, P,
+                                      C.POINTER(Report)]
     lib.dyson_profile.argtypes = [P, C.c_int]
     lib.dyson_profile_query.argtypes = [P, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     lib.dyson_set_chunk.argtypes = [P, C.c_int32]
@@ -227,6 +230,22 @@ class Solver:
         rep = Report()
         rc = self.lib.dyson_adjoint(self.h, w.ctypes.data, t_index, precision, tol, max_sweeps, C.byref(loss),
                                     gU.ctypes.data, gJ.ctypes.data, C.byref(rep))
+        self._check(rc, ok=allow)
+        return loss.value, gU, gJ[:self.p.Nb], SolveResult(rc, rep.as_dict())
+
+    def adjoint_obs(self, w_density=None, w_docc=None, t_index=None, precision=PREC_TF32X3_F64REF, tol=1e-11,
+                    max_sweeps=400, allow=(0,)):
+        """(loss, dL/dU, dL/dJ, SolveResult) of L = sum_i w_density_i n_i(t) + w_docc_i D_i(t)."""
+        t_index = self.p.Nt - 1 if t_index is None else t_index
+        wn = None if w_density is None else np.ascontiguousarray(np.asarray(w_density, dtype=np.float64))
+        wd = None if w_docc is None else np.ascontiguousarray(np.asarray(w_docc, dtype=np.float64))
+        loss = C.c_double()
+        gU = np.zeros((self.p.Nr, self.p.Nt))
+        gJ = np.zeros((max(self.p.Nb, 1), self.p.Nt))
+        rep = Report()
+        rc = self.lib.dyson_adjoint_obs(self.h, None if wn is None else wn.ctypes.data,
+                                        None if wd is None else wd.ctypes.data, t_index, precision, tol, max_sweeps,
+                                        C.byref(loss), gU.ctypes.data, gJ.ctypes.data, C.byref(rep))
         self._check(rc, ok=allow)
         return loss.value, gU, gJ[:self.p.Nb], SolveResult(rc, rep.as_dict())
 

@@ -681,19 +681,23 @@ int dyson_solve_vector_columns(dyson_ctx* c, const int32_t* sites, const int32_t
   return R.finish(status);
 }
 
-int dyson_adjoint(dyson_ctx* c, const double* w, int32_t t_index, int precision, double tol, int32_t max_sweeps,
-                  double* loss, double* grad_U, double* grad_J, dyson_report* rep_out) {
+int dyson_adjoint_obs(dyson_ctx* c, const double* w_density, const double* w_docc, int32_t t_index, int precision,
+                      double tol, int32_t max_sweeps, double* loss, double* grad_U, double* grad_J,
+                      dyson_report* rep_out) {
   if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
   ReportScope R(c, rep_out);
   int rc = check_solve_args(c, precision, tol, max_sweeps);
   if (rc) return R.finish(rc);
   if (c->sigma_transposed) return R.finish(ctx_fail(c, DYSON_ERR_STATE, "Lambda is transposed"));
-  if (!w || t_index < 0 || t_index >= c->Nt) return R.finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "bad weights or time"));
+  if ((!w_density && !w_docc) || t_index < 0 || t_index >= c->Nt || (w_docc && t_index < 1))
+    return R.finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "need weights, 0 <= t_index < Nt (>= 1 with D weights)"));
   DeviceGuard g(c->device);
   const int Nr = c->Nr, Nc = c->Nc, Nt = c->Nt;
-  const size_t colbuf = (size_t)Nr * Nr * Nc;                 // double2 elements of C (and R, gamma, rho)
-  const size_t need = (4 * colbuf + (size_t)Nr * Nc * Nc) * sizeof(double2) +
-                      ((size_t)Nr + 1 + (size_t)Nr * Nt + (size_t)std::max(c->Nb, 1) * Nt) * sizeof(double);
+  const bool docc = w_docc != nullptr;
+  const size_t colbuf = (size_t)Nr * Nr * Nc;                 // double2 elements of C (and the rows, psi, gamma, rho)
+  const size_t nbuf = docc ? 6 : 5;
+  const size_t need = (nbuf * colbuf + (size_t)Nr * Nc * Nc) * sizeof(double2) + (size_t)Nr * sizeof(AdjCoef) +
+                      ((size_t)3 * Nr + 1 + (size_t)Nr * Nt + (size_t)std::max(c->Nb, 1) * Nt) * sizeof(double);
   if (c->adj_bytes < need) {
     if (c->adj) cudaFree(c->adj);
     c->adj = nullptr;
@@ -706,25 +710,60 @@ int dyson_adjoint(dyson_ctx* c, const double* w, int32_t t_index, int precision,
     c->adj_bytes = need;
   }
   double2* C = (double2*)c->adj;
-  double2* Rw = C + colbuf;
-  double2* gam = Rw + colbuf;
+  double2* R1 = C + colbuf;
+  double2* R2 = docc ? R1 + colbuf : nullptr;
+  double2* psi = (docc ? R2 : R1) + colbuf;
+  double2* gam = psi + colbuf;
   double2* rho = gam + colbuf;
   double2* M = rho + colbuf;
-  double* w_dev = (double*)(M + (size_t)Nr * Nc * Nc);
-  double* loss_dev = w_dev + Nr;
+  AdjCoef* coef_dev = (AdjCoef*)(M + (size_t)Nr * Nc * Nc);
+  double* wn_dev = (double*)(coef_dev + Nr);
+  double* wd_dev = wn_dev + Nr;
+  double* ones_dev = wd_dev + Nr;
+  double* loss_dev = ones_dev + Nr;
   double* gU_dev = loss_dev + 1;
   double* gJ_dev = gU_dev + (size_t)Nr * Nt;
-  DY_CUDA(c, cudaMemcpyAsync(w_dev, w, Nr * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  std::vector<int32_t> sites(Nr), times(Nr, t_index);
-  for (int i = 0; i < Nr; ++i) sites[i] = i;
-  // columns G e_i and rows e_i^T G (columns of G^T) at (i, t_index) for every site
+  // coefficients beta'_i = i beta_i of the rows (see k_adjoint.cu): the density
+  // n_i = Im c_i(i, kf) gives b0 += w; the double occupancy D_i of Eq. (docc) gives
+  // b0 += i v / (dt U) - v eps / U, b1 = -i v / (dt U), bj = -v J_ij / U
+  std::vector<double> eps(Nr);
+  DY_CUDA(c, cudaMemcpyAsync(eps.data(), c->d_eps, Nr * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  std::vector<AdjCoef> coef(Nr);
+  std::vector<double> ones(Nr, 1.0);
+  for (int i = 0; i < Nr; ++i) {
+    AdjCoef& k = coef[i];
+    std::memset(&k, 0, sizeof k);
+    if (w_density) k.b0.x += w_density[i];
+    if (docc && w_docc[i] != 0.0) {
+      const double v = w_docc[i], U = c->U[(size_t)i * Nt + t_index];
+      k.b0.x += -v * eps[i] / U;
+      k.b0.y += v / (c->dt * U);
+      k.b1.y = -v / (c->dt * U);
+      for (int s = 0; s < 4; ++s)
+        if (c->h_nbr[i * 4 + s] >= 0) k.bj[s].x = -v * c->J[(size_t)c->h_nbond[i * 4 + s] * Nt + t_index] / U;
+    }
+  }
+  DY_CUDA(c, cudaMemcpyAsync(coef_dev, coef.data(), Nr * sizeof(AdjCoef), cudaMemcpyHostToDevice, c->stream));
+  DY_CUDA(c, cudaMemcpyAsync(ones_dev, ones.data(), Nr * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (w_density)
+    DY_CUDA(c, cudaMemcpyAsync(wn_dev, w_density, Nr * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  if (docc) DY_CUDA(c, cudaMemcpyAsync(wd_dev, w_docc, Nr * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  // columns G e_i at (i, kf); rows of G (columns of G^T) at (i, kf) and, for D, (i, kf - 1)
+  std::vector<int32_t> sites(2 * (size_t)Nr), times(2 * (size_t)Nr);
+  for (int i = 0; i < Nr; ++i) {
+    sites[i] = sites[Nr + i] = i;
+    times[i] = t_index;
+    times[Nr + i] = t_index - 1;
+  }
   dyson_report r1, r2;
   int st1 = dyson_solve_vector_columns(c, sites.data(), times.data(), Nr, precision, tol, max_sweeps,
                                        (double*)C, &r1);
   if (st1 != DYSON_OK && st1 != DYSON_ERR_NOT_CONVERGED) return R.finish(st1);
   if ((rc = dyson_transpose_sigma(c))) return R.finish(rc);
-  int st2 = dyson_solve_vector_columns(c, sites.data(), times.data(), Nr, precision, tol, max_sweeps,
-                                       (double*)Rw, &r2);
+  int st2 = dyson_solve_vector_columns(c, sites.data(), times.data(), docc ? 2 * Nr : Nr, precision, tol,
+                                       max_sweeps, (double*)R1, &r2);
   if ((rc = dyson_transpose_sigma(c))) return R.finish(rc);
   if (st2 != DYSON_OK && st2 != DYSON_ERR_NOT_CONVERGED) return R.finish(st2);
   R.rep.sweeps = r1.sweeps + r2.sweeps;
@@ -733,7 +772,10 @@ int dyson_adjoint(dyson_ctx* c, const double* w, int32_t t_index, int precision,
   R.rep.gemm_flops = r1.gemm_flops + r2.gemm_flops;
   R.rep.update = std::max(r1.update, r2.update);
   R.rep.residual = std::max(r1.residual, r2.residual);
-  if ((rc = adjoint_contract(c, C, Rw, w_dev, t_index, gam, rho, M, loss_dev, gU_dev, gJ_dev))) return R.finish(rc);
+  R.rep.inner_gmres = r1.inner_gmres | r2.inner_gmres;
+  if ((rc = adjoint_contract_obs(c, C, R1, R2, coef_dev, w_density ? wn_dev : nullptr, docc ? wd_dev : nullptr,
+                                 ones_dev, t_index, psi, gam, rho, M, loss_dev, gU_dev, gJ_dev)))
+    return R.finish(rc);
   if (loss) DY_CUDA(c, cudaMemcpyAsync(loss, loss_dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   if (grad_U)
     DY_CUDA(c, cudaMemcpyAsync(grad_U, gU_dev, (size_t)Nr * Nt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -744,6 +786,12 @@ int dyson_adjoint(dyson_ctx* c, const double* w, int32_t t_index, int precision,
   const int status = fold_status(st1, st2);
   if (status == DYSON_ERR_NOT_CONVERGED) ctx_fail(c, status, "max_sweeps or refinement limit reached above tolerance");
   return R.finish(status);
+}
+
+int dyson_adjoint(dyson_ctx* c, const double* w, int32_t t_index, int precision, double tol, int32_t max_sweeps,
+                  double* loss, double* grad_U, double* grad_J, dyson_report* rep_out) {
+  if (c && !w) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "bad weights or time");
+  return dyson_adjoint_obs(c, w, nullptr, t_index, precision, tol, max_sweeps, loss, grad_U, grad_J, rep_out);
 }
 
 int dyson_transpose_sigma(dyson_ctx* c) {

@@ -150,9 +150,16 @@ struct dyson_ctx {
 
 int ctx_fail(dyson_ctx* c, int code, const std::string& msg);
 
-// adjoint contractions (k_adjoint.cu): C, R columns of G and G^T at (i, zf) as [i][j][z]
-int adjoint_contract(dyson_ctx* c, const double2* C, const double2* R, const double* w_dev, int zf, double2* gam,
-                     double2* rho, double2* M, double* loss_dev, double* gU_dev, double* gJ_dev);
+// Adjoint of L = sum_i Re(beta_i . c_i) with beta'_i = i beta_i: per site i the
+// coefficient of the row at (i, kf) (b0), at (i, kf - 1) (b1) and at (j, kf) for
+// the neighbour in slot s (bj[s]).
+struct AdjCoef {
+  double2 b0, b1, bj[4];
+};
+int adjoint_contract_obs(dyson_ctx* c, const double2* C, const double2* R1, const double2* R2,
+                         const AdjCoef* coef_dev, const double* wn_dev, const double* wd_dev, const double* ones_dev,
+                         int kf, double2* psi, double2* gam, double2* rho, double2* M, double* loss_dev,
+                         double* gU_dev, double* gJ_dev);
 #define DY_CUDA(ctx, call)                                                              \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \

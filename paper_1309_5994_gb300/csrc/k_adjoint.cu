@@ -1,11 +1,15 @@
-// Gradients of L = sum_i w_i n_i(t_f), n_i(t_f) = Re[-i G_ii(z_f, z_f)] (no paper
-// counterpart).  From G = (I - K)^{-1} Lambda, K = Lambda W J:
-//     dG = (I + G W J) dLambda (I + W J G) + G W dJ G.
-// With the columns c_i = G e_i and rows r_i^T = e_i^T G (e_i the unit vector at
-// (i, z_f)); rows come from the same solver on transposed site blocks.
-//   dL/dJ_b(t_k) = sum_i w_i Im[sum_{z in Z_k} W(z) (r_i(l,z) c_i(m,z) + r_i(m,z) c_i(l,z))]
-//   dL/dU_l(t_k) = Re[-i sum_{z,z'} dLambda_l/dU_l(t_k)(z,z') M_l(z',z)],
-//     M_l = sum_i w_i gamma_i[l] rho_i[l]^T,  gamma_i = e_i + W J c_i,  rho_i = e_i + W J r_i.
+// Gradients of L = sum_i Re(beta_i . c_i), c_i = G e_i the column at (i, z_f) and
+// beta_i a sparse complex weight vector (no paper counterpart).  The site
+// density n_i(t_f) = Im c_i(i, z_f) and the double occupancy D_i(t_f) of
+// Eq. (docc) are both of this form.  From G = (I - K)^{-1} Lambda, K = Lambda W J:
+//     dG = (I + G W J) dLambda (I + W J G) + G W dJ G,
+// so with the effective rows psi_i = sum_a beta_ia r_a (r_a^T = e_a^T G: rows come
+// from the same solver on transposed site blocks), gamma_i = e_i + W J c_i and
+// rho_i = beta_i + W J psi_i:
+//   dL/dJ_b(t_k) = Re sum_i sum_{z in Z_k} W(z) (psi_i(l,z) c_i(m,z) + psi_i(m,z) c_i(l,z)),
+//   dL/dU_l(t_k) = Re sum_{z,z'} dLambda_l/dU_l(t_k)(z,z') M_l(z',z),  M_l = sum_i gamma_i[l] rho_i[l]^T,
+// plus D's explicit dependence on U(t_f), U(0) and J(t_f).  The kernels carry
+// beta' = i beta (real for the density) and take imaginary parts: Re(x) = Im(i x).
 // The derivative of the closed form (Sec. III): U(t_k), k >= 1, only moves the
 // channel-2 phase on real points later than t_k, so
 //   dL/dU_l(t_k) = -dt Re sum_{real z, m(z) > k} (rowsum_2 - colsum_2)(z),
@@ -13,7 +17,7 @@
 // U(0) also moves the level eps = V - U(0)/2 - mu, every phase and the Boltzmann
 // weights, and takes the full chain rule.
 //
-// Layouts: C, R [i][j][z] complex128 (column i of G or of G^T is [Nr][Nc]).
+// Layouts: C, rows and psi [i][j][z] complex128 (column i of G or of G^T is [Nr][Nc]).
 #include "common.cuh"
 
 namespace {
@@ -37,21 +41,6 @@ __device__ __forceinline__ void bond_sites(int b, int Lx, int Ly, int* l, int* m
 }
 
 // L = sum_i w_i Im C_i(i, z_f)
-__global__ void k_adj_loss(const double2* __restrict__ C, const double* __restrict__ w, int Nr, int Nc, int zf,
-                           double* __restrict__ loss) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < Nr; i += blockDim.x) s += w[i] * C[((size_t)i * Nr + i) * Nc + zf].y;
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ double part[32];
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x / 32] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += part[k];
-    *loss = t;
-  }
-}
-
 // one CTA per bond: gJ[b][k] = sum_i w_i Im[sum_{z in Z_k} W(z)(r_i(l,z) c_i(m,z) + r_i(m,z) c_i(l,z))]
 __global__ void k_adj_bonds(const double2* __restrict__ C, const double2* __restrict__ R, const double* __restrict__ w,
                             int Lx, int Ly, int Nt, int Nm, double dt, double beta, double* __restrict__ gJ) {
@@ -251,25 +240,118 @@ __global__ void k_adj_U(const double2* __restrict__ M, const double2* __restrict
   }
 }
 
+// Effective rows psi_i = sum_a beta'_ia r_a: rows at (i, kf), (i, kf - 1) and
+// (j, kf) for the neighbour slots j of i, with the coefficients of AdjCoef.
+// Layout [i][l][z]; one warp per (i, l).
+__global__ void k_adj_psi(const double2* __restrict__ R1, const double2* __restrict__ R2,
+                          const AdjCoef* __restrict__ coef, const int* __restrict__ nbr, int Nr, int Nc,
+                          double2* __restrict__ psi) {
+  const size_t il = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  if (il >= (size_t)Nr * Nr) return;
+  const int i = (int)(il / Nr), l = (int)(il % Nr);
+  const AdjCoef cf = coef[i];
+  int js[4];
+  for (int s = 0; s < 4; ++s) js[s] = nbr[i * 4 + s];
+  for (int z = threadIdx.x & 31; z < Nc; z += 32) {
+    double2 acc = cmul(cf.b0, R1[((size_t)i * Nr + l) * Nc + z]);
+    if (R2) {
+      const double2 t = cmul(cf.b1, R2[((size_t)i * Nr + l) * Nc + z]);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    for (int s = 0; s < 4; ++s) {
+      if (js[s] < 0 || (cf.bj[s].x == 0.0 && cf.bj[s].y == 0.0)) continue;
+      const double2 t = cmul(cf.bj[s], R1[((size_t)js[s] * Nr + l) * Nc + z]);
+      acc.x += t.x;
+      acc.y += t.y;
+    }
+    psi[il * Nc + z] = acc;
+  }
+}
+
+// rho_i += beta'_i (its few non-zero entries); rho layout [l][i][z]
+__global__ void k_adj_rho_add(const AdjCoef* __restrict__ coef, const int* __restrict__ nbr, int Nr, int Nc, int kf,
+                              double2* __restrict__ rho) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nr) return;
+  const AdjCoef cf = coef[i];
+  auto add = [&](int l, int z, double2 v) {
+    double2& r = rho[((size_t)l * Nr + i) * Nc + z];
+    r.x += v.x;
+    r.y += v.y;
+  };
+  add(i, kf, cf.b0);
+  if (kf >= 1) add(i, kf - 1, cf.b1);
+  for (int s = 0; s < 4; ++s)
+    if (nbr[i * 4 + s] >= 0) add(nbr[i * 4 + s], kf, cf.bj[s]);
+}
+
+// Loss L = sum_i wn_i n_i + wd_i D_i from the columns, and the explicit dependence
+// of D_i on U_i(t_f), U_i(0) (through eps_i) and J_ij(t_f), added to gU and gJ.
+__global__ void k_adj_obs_terms(const double2* __restrict__ C, const double* __restrict__ wn,
+                                const double* __restrict__ wd, const double* __restrict__ eps,
+                                const double* __restrict__ Utab, const double* __restrict__ Jtab,
+                                const int* __restrict__ nbr, const int* __restrict__ nbond, int Nr, int Nt, int Nc,
+                                int kf, double dt, double* __restrict__ loss, double* __restrict__ gU,
+                                double* __restrict__ gJ) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < Nr; i += blockDim.x) {
+    const double2* ci = C + (size_t)i * Nr * Nc;
+    const double n = ci[(size_t)i * Nc + kf].y;
+    if (wn) s += wn[i] * n;
+    if (wd && wd[i] != 0.0) {
+      const double U = Utab[(size_t)i * Nt + kf];
+      double ekin = 0.0;
+      for (int q = 0; q < 4; ++q) {
+        const int j = nbr[i * 4 + q];
+        if (j >= 0) ekin += Jtab[(size_t)nbond[i * 4 + q] * Nt + kf] * ci[(size_t)j * Nc + kf].y;
+      }
+      const double D = ((ci[(size_t)i * Nc + kf].x - ci[(size_t)i * Nc + kf - 1].x) / dt - eps[i] * n - ekin) / U;
+      s += wd[i] * D;
+      atomicAdd(&gU[(size_t)i * Nt + kf], wd[i] * (-D / U));
+      atomicAdd(&gU[(size_t)i * Nt + 0], wd[i] * n / (2.0 * U));
+      for (int q = 0; q < 4; ++q) {
+        const int j = nbr[i * 4 + q];
+        if (j >= 0) atomicAdd(&gJ[(size_t)nbond[i * 4 + q] * Nt + kf], wd[i] * (-ci[(size_t)j * Nc + kf].y / U));
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double part[32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x / 32); ++k) t += part[k];
+    *loss = t;
+  }
+}
+
 }  // namespace
 
-int adjoint_contract(dyson_ctx* c, const double2* C, const double2* R, const double* w_dev, int zf, double2* gam,
-                     double2* rho, double2* M, double* loss_dev, double* gU_dev, double* gJ_dev) {
+int adjoint_contract_obs(dyson_ctx* c, const double2* C, const double2* R1, const double2* R2,
+                         const AdjCoef* coef_dev, const double* wn_dev, const double* wd_dev, const double* ones_dev,
+                         int kf, double2* psi, double2* gam, double2* rho, double2* M, double* loss_dev,
+                         double* gU_dev, double* gJ_dev) {
   const int Nr = c->Nr, Nc = c->Nc, Nt = c->Nt;
-  k_adj_loss<<<1, 256, 0, c->stream>>>(C, w_dev, Nr, Nc, zf, loss_dev);
-  if (c->Nb > 0)
-    k_adj_bonds<<<c->Nb, 256, Nt * sizeof(double), c->stream>>>(C, R, w_dev, c->Lx, c->Ly, Nt, c->Nm, c->dt,
-                                                                  c->beta, gJ_dev);
   const size_t warps = (size_t)Nr * Nr;
-  k_adj_gather<<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(C, c->d_nbr, c->d_nbond, c->dJ, Nr, Nt, c->Nm,
-                                                                  c->dt, c->beta, zf, gam);
-  k_adj_gather<<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(R, c->d_nbr, c->d_nbond, c->dJ, Nr, Nt, c->Nm,
-                                                                  c->dt, c->beta, zf, rho);
+  const unsigned wblocks = (unsigned)((warps + 7) / 8);
+  k_adj_psi<<<wblocks, 256, 0, c->stream>>>(R1, R2, coef_dev, c->d_nbr, Nr, Nc, psi);
+  if (c->Nb > 0)
+    k_adj_bonds<<<c->Nb, 256, Nt * sizeof(double), c->stream>>>(C, psi, ones_dev, c->Lx, c->Ly, Nt, c->Nm, c->dt,
+                                                                  c->beta, gJ_dev);
+  k_adj_gather<<<wblocks, 256, 0, c->stream>>>(C, c->d_nbr, c->d_nbond, c->dJ, Nr, Nt, c->Nm, c->dt, c->beta, kf,
+                                               gam);
+  k_adj_gather<<<wblocks, 256, 0, c->stream>>>(psi, c->d_nbr, c->d_nbond, c->dJ, Nr, Nt, c->Nm, c->dt, c->beta, -1,
+                                               rho);
+  k_adj_rho_add<<<(Nr + 127) / 128, 128, 0, c->stream>>>(coef_dev, c->d_nbr, Nr, Nc, kf, rho);
   const int tiles = (Nc + 31) / 32;
-  k_adj_M<<<dim3(tiles, tiles, Nr), 256, 0, c->stream>>>(gam, rho, w_dev, Nr, Nc, M);
+  k_adj_M<<<dim3(tiles, tiles, Nr), 256, 0, c->stream>>>(gam, rho, ones_dev, Nr, Nc, M);
   const size_t shmem = (size_t)(Nc + Nt + 64) * sizeof(double);
   k_adj_U<<<Nr, 256, shmem, c->stream>>>(M, c->d_phase, Nt, c->Nm, c->dt, c->beta, gU_dev);
-  c->launches += (c->Nb > 0 ? 6 : 5);
+  k_adj_obs_terms<<<1, 256, 0, c->stream>>>(C, wn_dev, wd_dev, c->d_eps, c->dU, c->dJ, c->d_nbr, c->d_nbond, Nr, Nt,
+                                            Nc, kf, c->dt, loss_dev, gU_dev, gJ_dev);
+  c->launches += (c->Nb > 0 ? 9 : 8);
   DY_CUDA(c, cudaGetLastError());
   return DYSON_OK;
 }

@@ -78,6 +78,44 @@ def test_adjoint_matches_oracle(torch_cuda, lib, kw):
         assert np.abs(gJg - gJ).max() < 1e-10 * max(1.0, np.abs(gJ).max())
 
 
+@pytest.mark.parametrize("kw", CASES[:2])
+def test_density_and_double_occupancy_adjoint_matches_oracle(torch_cuda, lib, kw):
+    """L = sum_i w_i n_i(t) + v_i D_i(t) at an inner forward time: loss and
+    gradients against the oracle's adjoint, FP64 and mixed paths."""
+    p = wl.random_tables(wl.small(**kw), seed=29, rel=0.15)
+    rng = np.random.default_rng(6)
+    w, v = rng.uniform(0, 1, p.Nr), rng.uniform(0, 1, p.Nr)
+    kf = p.Nt - 2
+    L, gU, gJ = adjoint.obs_gradients(p, w=w, v=v, t_index=kf)
+    s = _solver(p)
+    for prec in (0, 1):
+        Lg, gUg, gJg, res = s.adjoint_obs(w, v, t_index=kf, precision=prec, tol=1e-13)
+        assert abs(Lg - L) < 1e-11 * max(1.0, abs(L))
+        assert np.abs(gUg - gU).max() < 1e-9 * max(1.0, np.abs(gU).max())
+        assert np.abs(gJg - gJ).max() < 1e-9 * max(1.0, np.abs(gJ).max())
+    # double occupancies alone
+    Ld, gUd, gJd = adjoint.obs_gradients(p, v=v, t_index=kf)
+    Lg, gUg, gJg, _ = s.adjoint_obs(None, v, t_index=kf, precision=1, tol=1e-13)
+    assert abs(Lg - Ld) < 1e-11 * max(1.0, abs(Ld))
+    assert np.abs(gUg - gUd).max() < 1e-9 * max(1.0, np.abs(gUd).max())
+
+
+def test_double_occupancy_amplitude_gradient_matches_finite_differences(torch_cuda, lib):
+    """Drive amplitude s (reading 12): d/ds of sum_i v_i D_i(t_final) from the GPU
+    adjoint through the chain rule against central differences of the GPU loss."""
+    kw = dict(L=2, Ly=3, Nt=24, Nm=16, dt=0.05, trap_c=0.3, U0=20.0, aU=0.1, aJ=0.2, omega=20.0)
+    v = np.random.default_rng(12).uniform(0, 1, 6)
+    base = wl.small(**kw, amp=1.0)
+    s = _solver(base)
+    _, gU, gJ, _ = s.adjoint_obs(None, v, precision=1, tol=1e-13)
+    dU, dJ = wl.drive_derivative_tables(base)
+    chain = float(np.sum(gU * dU) + np.sum(gJ * dJ))
+    h = 1e-4
+    vals = [_solver(wl.small(**kw, amp=a)).adjoint_obs(None, v, precision=1, tol=1e-13)[0] for a in (1 + h, 1 - h)]
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert abs(fd - chain) < 1e-6 * max(abs(fd), 1e-3), (fd, chain)
+
+
 def test_autograd_amplitude_gradient(torch_cuda, lib):
     """The drive built from a torch scalar s: s.grad through torch.autograd equals
     the oracle's chain rule of its adjoint gradients."""
