@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batch", type=int, default=16, help="block columns per step per GPU")
-    ap.add_argument("--tol", type=float, default=1e-10, help="relative FP64 Dyson residual")
+    ap.add_argument("--tol", type=float, default=1e-8,
+                    help="relative FP64 Dyson residual (the metric is quoted at relative error 1e-6)")
     ap.add_argument("--f64-columns", type=int, default=2, help="block columns timed on the plain FP64 path")
     ap.add_argument("--cpu-columns", type=int, default=32, help="vector columns in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU legs (profiling runs)")
@@ -141,15 +142,15 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle legs
 # ---------------------------------------------------------------------------
-def oracle_sample(p, site: int, zps, S=None):
-    """Time the CPU oracle's complex128 series on vector columns (site, z') of p."""
+def oracle_sample(p, site: int, zps, tol: float, S=None):
+    """Time the CPU oracle's complex128 series on vector columns (site, z') of p,
+    stopped at the relative update tol."""
     from oracle import dyson
     if S is None:
         S = dyson.setup(p)
     B = dyson.rhs_vector_columns(S, [(site, int(z)) for z in zps])
     t = time.perf_counter()
-    # 1e-12: the complex128 series' update settles near 1e-13 on this contour
-    G, sweeps, _ = dyson.neumann_solve(S, B, tol=1e-12, max_sweeps=400)
+    G, sweeps, _ = dyson.neumann_solve(S, B, tol=tol, max_sweeps=400)
     dt = time.perf_counter() - t
     return dt, sweeps, S
 
@@ -165,13 +166,13 @@ def blas_threads() -> int:
     return os.cpu_count() or 1
 
 
-def cpu_baseline(p, ncols: int):
+def cpu_baseline(p, ncols: int, tol: float):
     import numpy as np
     zps = np.linspace(0, p.Nc - 1, ncols).astype(int)
-    dt, sweeps, _ = oracle_sample(p, 119, zps)
+    dt, sweeps, _ = oracle_sample(p, 119, zps, tol)
     per_block = dt * p.Nc / ncols
     return {"value": 1.0 / per_block, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-            "sample": (f"{ncols} of the 256 vector columns of block column 119, complex128 series to 1e-12 "
+            "sample": (f"{ncols} of the 256 vector columns of block column 119, complex128 series to {tol:g} "
                        f"({sweeps} sweeps, {dt:.2f} s), scaled linearly to one block column")}
 
 
@@ -307,7 +308,7 @@ def run_reference(args, rank, world):
     for step in range(args.warmup + args.steps):
         site = (step * 37) % p.Nr
         zps = np.linspace(step % 16, p.Nc - 1, ncols).astype(int)
-        dt, _, _ = oracle_sample(p, site, zps, S)
+        dt, _, _ = oracle_sample(p, site, zps, args.tol, S)
         if step >= args.warmup:
             times.append(dt * p.Nc / ncols)      # seconds per block column
     per_block = sum(times) / len(times)
@@ -317,7 +318,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": WORKLOAD, "step": f"{ncols} vector columns of one block column"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                             "sample": f"{ncols} vector columns per step, complex128 series, scaled to block columns"},
+                             "sample": f"{ncols} vector columns per step, complex128 series to {args.tol:g}, "
+                                       "scaled to block columns"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -456,14 +458,21 @@ def run_gb300(args, rank, world, local):
             g64 = torch.empty((nf, Nr, Nc, Nc), dtype=torch.complex128, device=dev)
             gmx = torch.empty_like(g64)
             solver.build_sigma()
+            # timed: the FP64 series stopped at the same relative level as the mixed path
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            # the FP64 series update bottoms out near 1e-13 on this contour (rounding of
-            # partial sums that peak ~200x above the result), so 1e-12 is its reachable target
-            r64 = solver.solve(srcs, precision=binding.PREC_F64, tol=1e-12, max_sweeps=400, g_out=g64,
+            r64 = solver.solve(srcs, precision=binding.PREC_F64, tol=args.tol, max_sweeps=400, g_out=g64,
                                allow=(0, -3))
             torch.cuda.synchronize(dev)
             t64 = time.perf_counter() - t0
+            # the accuracy reference: the FP64 series to 1e-12 (its update bottoms out near
+            # 1e-13 on this contour, partial sums peaking ~200x above the result)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            r64t = solver.solve(srcs, precision=binding.PREC_F64, tol=1e-12, max_sweeps=400, g_out=g64,
+                                allow=(0, -3))
+            torch.cuda.synchronize(dev)
+            t64t = time.perf_counter() - t0
             n64, _, _ = solver.observables()
             rmx = solver.solve(srcs, precision=PREC, tol=args.tol, max_sweeps=400, g_out=gmx)
             nmx, _, _ = solver.observables()
@@ -474,15 +483,19 @@ def run_gb300(args, rank, world, local):
             gii_err = (torch.abs(gii_m - gii).max() / torch.abs(gii).max()).item()
             nerr = float(np.abs(nmx[srcs] - n64[srcs]).max() / np.abs(n64[srcs]).max())
             f64_rate = nf / t64
-            extras["plain_f64"] = {"value": f64_rate, "unit": UNIT, "block_columns": nf,
+            extras["plain_f64"] = {"value": f64_rate, "unit": UNIT, "block_columns": nf, "tol_rel_update": args.tol,
                                    "sweeps": r64.report["sweeps"], "status": r64.status,
                                    "final_update": r64.report["update"],
-                                   "tflops": r64.report["gemm_flops"] / t64 / 1e12}
+                                   "tflops": r64.report["gemm_flops"] / t64 / 1e12,
+                                   "tight": {"tol_rel_update": 1e-12, "value": nf / t64t, "unit": UNIT,
+                                             "sweeps": r64t.report["sweeps"], "status": r64t.status,
+                                             "final_update": r64t.report["update"]}}
             extras["speedup_vs_plain_f64"] = (value / world) / f64_rate
-            extras["rel_err_vs_plain_f64"] = {"G": gerr, "G_ii": gii_err, "density": nerr}
+            extras["rel_err_vs_plain_f64"] = {"reference": "FP64 series to 1e-12", "G": gerr, "G_ii": gii_err,
+                                              "density": nerr}
             del g64, gmx
             if world == 1:
-                extras["cpu_baseline"] = cpu_baseline(p, args.cpu_columns)
+                extras["cpu_baseline"] = cpu_baseline(p, args.cpu_columns, args.tol)
             if args.uneven_instances > 0:
                 extras["batched_uneven"] = batched_uneven_leg(args, dev, stream)
             if not args.no_driven:

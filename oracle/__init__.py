@@ -22,10 +22,12 @@ dyson        Sec. IV.D, Eqs. (Glatt2)/(Ginvblockstruct), App. C: the lattice
              series in powers of J, and in the sine basis for homogeneous
              lattices.
 observables  Sec. III.A and App. B: density, kinetic energy, double occupancy.
-adjoint      Gradients of a weighted density sum (no counterpart in the paper;
-             derived from the Dyson equation).
+adjoint      Gradients of weighted densities and double occupancies (no
+             counterpart in the paper; derived from the Dyson equation).
+extrapolate  Sec. IV.D: quadratic (or linear) extrapolation of results on
+             refined contours to step 0.
 
 Parity status of every function is stated in its docstring; functions whose
 results are not fixed by an independent pin say "parity unpinned".
 """
-from . import contour, lattice, atomic, dyson, observables, adjoint  # noqa: F401
+from . import contour, lattice, atomic, dyson, observables, adjoint, extrapolate  # noqa: F401

@@ -156,6 +156,24 @@ def small(name="small", L=3, Nt=6, Nm=4, dt=0.1, beta=1.0, mu=0.0, trap_c=0.3, U
     return uniform_problem(name, L, Nt, Nm, dt, beta, mu, trap_c, U0, J0, Ly=Ly, **drive)
 
 
+def refine(p: Problem, m: int) -> Problem:
+    """The same uniform_problem on a contour whose step is divided by the integer m.
+
+    The real-time grid keeps its final time, (Nt - 1)*dt = (Nt' - 1)*dt/m, so
+    Nt' = m*(Nt - 1) + 1, and the imaginary branch gets m*Nm points; the drive
+    tables are resampled from the drive parameters.  Time t_k of p is index m*k
+    of the refined problem.
+    """
+    if m < 1 or int(m) != m:
+        raise ValueError("m must be a positive integer")
+    if "U0" not in p.meta:
+        raise ValueError("refine needs a uniform_problem (its drive parameters)")
+    d = p.meta
+    return uniform_problem(f"{p.name}_dt/{m}", p.Lx, m * (p.Nt - 1) + 1, m * p.Nm, p.dt / m, p.beta, p.mu,
+                           p.trap_c, d["U0"], d["J0"], Ly=p.Ly, aU=d["aU"], aJ=d["aJ"], omega=d["omega"],
+                           phase=d["phase"], amp=d["amp"])
+
+
 def random_tables(p: Problem, seed: int, rel: float = 0.1) -> Problem:
     """Perturb every site's U and every bond's J independently (breaks all lattice symmetry)."""
     rng = np.random.default_rng(seed)
