@@ -194,6 +194,30 @@ int dyson_adjoint_obs(dyson_ctx* ctx, const double* w_density, const double* w_d
  * on_device != 0 means the pointers are device memory, else host memory. */
 int dyson_observables(dyson_ctx* ctx, double* n, double* ekin, double* docc, int on_device);
 
+/* Delta t -> 0 extrapolation (Sec. IV.D).  The same tables computed on n_grids
+ * contours whose steps are h_b = h_0 / m_b (integer divisors, m_0 = 1 < m_1 <
+ * ...; the real-time grid of contour b has at least m_b (nt[0] - 1) + 1
+ * points, e.g. m_b nt[0] with m_b times the points on every branch) are
+ * combined at the coarsest grid's times
+ * t_k = k h_0, which are index k m_b of grid b, with the weights of the
+ * polynomial of degree n_grids - 1 through the points (h_b, f_b) evaluated at
+ * h = 0 (Lagrange form):
+ *     out[r][k] = sum_b values[b][r][k m_b] prod_{c != b} h_c / (h_c - h_b).
+ * n_grids = 3 is the paper's quadratic extrapolation, 2 the linear one it
+ * cross-checks with.
+ *   values  host array of n_grids DEVICE pointers; values[b] is [rows][nt[b]]
+ *           doubles (e.g. a table of dyson_observables on the context of grid b);
+ *   nt      host, [n_grids] time points per row;  m  host, [n_grids] divisors;
+ *   out     device, [rows][nt[0]] doubles (may not alias an input).
+ * NaN inputs (D at t = 0) give NaN.  Runs on `stream` (NULL: the legacy default
+ * stream) of `device`.  Returns DYSON_ERR_INVALID_ARG for n_grids outside 1..4,
+ * divisors that do not start at 1 or do not increase, a grid shorter than
+ * m_b (nt[0] - 1) + 1, rows < 1 or a NULL pointer (message in
+ * dyson_last_error(NULL)), DYSON_ERR_CUDA if the launch fails. */
+#define DYSON_EXTRAPOLATE_MAX_GRIDS 4
+int dyson_extrapolate_dt(int32_t n_grids, const double* const* values, const int32_t* nt, const int32_t* m,
+                         int32_t rows, double* out, int device, void* stream);
+
 void dyson_destroy(dyson_ctx* ctx);
 const char* dyson_last_error(const dyson_ctx* ctx);
 

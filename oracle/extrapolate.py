@@ -13,9 +13,9 @@ the points (h_b, f_b), evaluated at 0, is the Lagrange sum
     f(0) = sum_b f_b L_b(0),   L_b(0) = prod_{c != b} h_c / (h_c - h_b).
 
 Reading (the paper does not say how the grids are refined): step b divides the
-coarsest step by an integer, h_b = h_0 / m_b, and refines the whole contour, the
-real-time grid up to the same final time and the imaginary branch with m_b
-times the points (workloads.refine).  Results are compared at the coarsest
+coarsest step by an integer, h_b = h_0 / m_b, and refines the whole contour,
+every branch with m_b times the points (workloads.refine); the real-time grid
+then covers the coarse grid's times.  Results are compared at the coarsest
 grid's times t_k = k h_0, which are index k m_b of grid b.
 
 Parity: pinned by the textbook Richardson weights, by exactness on polynomial

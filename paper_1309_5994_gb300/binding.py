@@ -73,7 +73,7 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
            "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune", "dyson_set_symmetry",
-           "dyson_adjoint_obs"]
+           "dyson_adjoint_obs", "dyson_extrapolate_dt"]
 SYMMETRY_NONE, SYMMETRY_C4V = 0, 1
 INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
@@ -128,6 +128,8 @@ def load(path: str = _LIB_PATH):
     lib.dyson_last_error.argtypes = [P]
     lib.dyson_last_error.restype = C.c_char_p
     lib.dyson_version.restype = C.c_char_p
+    lib.dyson_extrapolate_dt.argtypes = [C.c_int32, C.POINTER(P), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                         C.c_int32, P, C.c_int, P]
     _lib = lib
     return lib
 
@@ -136,6 +138,33 @@ class DysonError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
         self.code = code
+
+
+def extrapolate_dt(tables, m, out=None, stream=None):
+    """Delta t -> 0 extrapolation (dyson_extrapolate_dt) of float64 device tensors
+    tables[b] of shape [rows, nt_b] computed on contours of step h_0 / m[b];
+    returns out, [rows, nt_0] on the device of tables[0]."""
+    import torch
+    lib = load()
+    n = len(tables)
+    t0 = tables[0]
+    for t in tables:
+        if t.dtype != torch.float64 or not t.is_cuda or t.dim() != 2 or not t.is_contiguous():
+            raise ValueError("tables must be contiguous 2-D float64 CUDA tensors")
+        if t.shape[0] != t0.shape[0] or t.device != t0.device:
+            raise ValueError("tables must share rows and device")
+    if out is None:
+        out = torch.empty_like(t0)
+    if stream is None:
+        stream = torch.cuda.current_stream(t0.device)
+    ptrs = (C.c_void_p * n)(*[t.data_ptr() for t in tables])
+    nt = (C.c_int32 * n)(*[t.shape[1] for t in tables])
+    mm = (C.c_int32 * n)(*[int(x) for x in m])
+    rc = lib.dyson_extrapolate_dt(n, ptrs, nt, mm, t0.shape[0], C.c_void_p(out.data_ptr()), t0.device.index,
+                                  C.c_void_p(stream.cuda_stream))
+    if rc != 0:
+        raise DysonError(rc, lib.dyson_last_error(None).decode())
+    return out
 
 
 @dataclass

@@ -34,9 +34,22 @@ def test_polynomial_data_is_reproduced_exactly(ms):
 def test_refined_grid_keeps_the_final_time_and_the_drive():
     p = wl.small(L=2, Ly=2, Nt=9, Nm=4, dt=0.1, aU=0.1, aJ=0.2, omega=5.0)
     q = wl.refine(p, 4)
-    assert (q.Nt, q.Nm, q.dt) == (33, 16, 0.025)
-    assert (q.Nt - 1) * q.dt == pytest.approx((p.Nt - 1) * p.dt)
+    assert (q.Nt, q.Nm, q.dt, q.Nc) == (36, 16, 0.025, 4 * p.Nc)
     assert np.array_equal(q.U[:, ::4], p.U) and np.array_equal(q.J[:, ::4], p.J)
+
+
+def test_points_past_the_coarse_grid_leave_the_observables_unchanged():
+    """The refined grid runs m - 1 points past the coarse grid's last time; by the t_max
+    independence of the contour the observables at the coarse times are those of a grid
+    that stops there."""
+    p = wl.small(L=2, Ly=2, Nt=6, Nm=4, dt=0.1, aU=0.1, aJ=0.2, omega=5.0)
+    q = wl.refine(p, 2)
+    short = wl.uniform_problem("short", 2, 2 * p.Nt - 1, 2 * p.Nm, p.dt / 2, p.beta, p.mu, p.trap_c, 8.0, 1.0,
+                               Ly=2, aU=0.1, aJ=0.2, omega=5.0)
+    a = ex.observables_dense(q)
+    b = ex.observables_dense(short)
+    for x, y in zip(a, b):
+        assert np.allclose(x[:, : short.Nt], y, rtol=0, atol=1e-12, equal_nan=True)
 
 
 def test_extrapolated_observables_converge_at_third_order():

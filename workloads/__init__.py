@@ -159,17 +159,18 @@ def small(name="small", L=3, Nt=6, Nm=4, dt=0.1, beta=1.0, mu=0.0, trap_c=0.3, U
 def refine(p: Problem, m: int) -> Problem:
     """The same uniform_problem on a contour whose step is divided by the integer m.
 
-    The real-time grid keeps its final time, (Nt - 1)*dt = (Nt' - 1)*dt/m, so
-    Nt' = m*(Nt - 1) + 1, and the imaginary branch gets m*Nm points; the drive
-    tables are resampled from the drive parameters.  Time t_k of p is index m*k
-    of the refined problem.
+    Every branch gets m times the points (Nt' = m*Nt, Nm' = m*Nm, so Nc' = m*Nc):
+    the real-time grid covers the times of p (t_k of p is index m*k) and m - 1
+    finer points past its last one, which leave the results at earlier times
+    unchanged (the t_max independence of the contour).  The drive tables are
+    resampled from the drive parameters.
     """
     if m < 1 or int(m) != m:
         raise ValueError("m must be a positive integer")
     if "U0" not in p.meta:
         raise ValueError("refine needs a uniform_problem (its drive parameters)")
     d = p.meta
-    return uniform_problem(f"{p.name}_dt/{m}", p.Lx, m * (p.Nt - 1) + 1, m * p.Nm, p.dt / m, p.beta, p.mu,
+    return uniform_problem(f"{p.name}_dt/{m}", p.Lx, m * p.Nt, m * p.Nm, p.dt / m, p.beta, p.mu,
                            p.trap_c, d["U0"], d["J0"], Ly=p.Ly, aU=d["aU"], aJ=d["aJ"], omega=d["omega"],
                            phase=d["phase"], amp=d["amp"])
 
