@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--batch", type=int, default=16, help="block columns per step per GPU")
-    ap.add_argument("--tol", type=float, default=1e-8,
-                    help="relative FP64 Dyson residual (the metric is quoted at relative error 1e-6)")
+    ap.add_argument("--tol", type=float, default=1e-7,
+                    help="relative FP64 Dyson residual (the metric is quoted at relative error 1e-6; the "
+                         "errors of the result against the FP64 series to 1e-12 are measured and reported)")
     ap.add_argument("--f64-columns", type=int, default=2, help="block columns timed on the plain FP64 path")
     ap.add_argument("--cpu-columns", type=int, default=32, help="vector columns in the CPU oracle sample")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, FP64 and CPU legs (profiling runs)")
@@ -492,7 +493,7 @@ def run_gb300(args, rank, world, local):
                                              "final_update": r64t.report["update"]}}
             extras["speedup_vs_plain_f64"] = (value / world) / f64_rate
             extras["rel_err_vs_plain_f64"] = {"reference": "FP64 series to 1e-12", "G": gerr, "G_ii": gii_err,
-                                              "density": nerr}
+                                              "density": nerr, "within_1e-6": bool(max(gii_err, nerr) <= 1e-6)}
             del g64, gmx
             if world == 1:
                 extras["cpu_baseline"] = cpu_baseline(p, args.cpu_columns, args.tol)

@@ -306,6 +306,17 @@ int dyson_autotune(dyson_ctx* ctx, int32_t max_block_columns, dyson_tuning* out)
 enum { DYSON_INNER_SERIES = 0, DYSON_INNER_GMRES = 1, DYSON_INNER_AUTO = 2 };
 int dyson_set_inner_solver(dyson_ctx* ctx, int solver, int32_t restart);
 
+/* Support truncation (Sec. IV.D: the iterates spread from the localised start
+ * one hop per application of the hopping).  The first right-hand side of a
+ * solve, Lambda delta_s, is non-zero only on each column's source site, so after
+ * n series sweeps a column vanishes beyond lattice distance n of its source.
+ * When enabled (the default), the first inner series of the mixed-precision path
+ * on the tensor cores skips every (site, 256-column) tile that is still zero:
+ * the results are bit-identical, the work of the early sweeps shrinks.  Later
+ * refinements (whose residuals are dense), GMRES, the FP64 and the CUDA-core FP32
+ * sweeps are not truncated.  Truncated sweeps use the single-CTA kernel. */
+int dyson_set_support_truncation(dyson_ctx* ctx, int enable);
+
 /* ---------------------------------------------------------------------------
  * Batched solves of several problem instances.  The paper solves one trap at a
  * time; this entry point serves scans over many traps, lattices and drives.

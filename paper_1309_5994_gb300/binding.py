@@ -73,7 +73,7 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
            "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune", "dyson_set_symmetry",
-           "dyson_adjoint_obs", "dyson_extrapolate_dt"]
+           "dyson_adjoint_obs", "dyson_extrapolate_dt", "dyson_set_support_truncation"]
 SYMMETRY_NONE, SYMMETRY_C4V = 0, 1
 INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
@@ -108,6 +108,7 @@ def load(path: str = _LIB_PATH):
     lib.dyson_set_inner_solver.argtypes = [P, C.c_int, C.c_int32]
     lib.dyson_autotune.argtypes = [P, C.c_int32, C.POINTER(Tuning)]
     lib.dyson_set_symmetry.argtypes = [P, C.c_int]
+    lib.dyson_set_support_truncation.argtypes = [P, C.c_int]
     lib.dyson_launch_count.argtypes = [P]
     lib.dyson_launch_count.restype = C.c_int64
     lib.dyson_solve_block_column_noalloc.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
@@ -309,6 +310,9 @@ class Solver:
 
     def set_inner_solver(self, solver: int, restart: int = 0):
         self._check(self.lib.dyson_set_inner_solver(self.h, solver, restart))
+
+    def set_support_truncation(self, enable: bool):
+        self._check(self.lib.dyson_set_support_truncation(self.h, 1 if enable else 0))
 
     def set_sweep_variant(self, variant: int):
         self._check(self.lib.dyson_set_sweep_variant(self.h, variant))

@@ -183,12 +183,15 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
 }
 
 // inner solve d <- r + K d in FP32 (SIMT or 3xTF32 tensor cores)
+// act (optional): support truncation of the tensor-core sweeps (tc_sweep), valid
+// while every column of r32 is zero off its source site
 int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float* da, float* db, int max_sweeps,
                 const std::vector<double>& rref, float** dres, dyson_report* rep, double* peak_out,
-                double abort_peak = std::numeric_limits<double>::infinity()) {
+                double abort_peak = std::numeric_limits<double>::infinity(), const int* act = nullptr) {
   const int ng = ncol / gs;
   const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
   DY_CUDA(c, cudaMemcpyAsync(da, r32, n32 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+  if (act) DY_CUDA(c, cudaMemsetAsync(db, 0, n32 * sizeof(float), c->stream));   // skipped tiles stay 0
   double best = std::numeric_limits<double>::infinity(), peak = 0.0;
   int since_best = 0, rc;
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
@@ -196,10 +199,10 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
     if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
       {
         KernelTimer t(c, DYSON_KERNEL_GATHER_TC);
-        if ((rc = tc_sweep(c, ncol, gs, r32, da, db, TC_GATHER))) return rc;
+        if ((rc = tc_sweep(c, ncol, gs, r32, da, db, TC_GATHER, act, sweep))) return rc;
       }
-      KernelTimer t(c, tc_uses_pair(c) ? DYSON_KERNEL_SWEEP_TC_PAIR : DYSON_KERNEL_SWEEP_TC);
-      if ((rc = tc_sweep(c, ncol, gs, r32, da, db, TC_GEMM))) return rc;
+      KernelTimer t(c, tc_uses_pair(c) && !act ? DYSON_KERNEL_SWEEP_TC_PAIR : DYSON_KERNEL_SWEEP_TC);
+      if ((rc = tc_sweep(c, ncol, gs, r32, da, db, TC_GEMM, act, sweep))) return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
       launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, ncol, gs,
@@ -259,6 +262,52 @@ int matvec_f32(dyson_ctx* c, int ncol, int gs, int precision, const float* zero,
   return DYSON_OK;
 }
 
+// Support truncation (NEXT-2 of the build plan; Sec. IV.D): the first right-hand
+// side Lambda delta_s is non-zero only on the source site of each column, and a
+// sweep spreads an iterate by one hop, so after n sweeps a column is zero beyond
+// lattice distance n of its source.  act[i][t] = min over the columns of 256-column
+// tile t of the distance from site i to the column's source: the first sweep at
+// which the tile can be non-zero.  Uploaded to c->d_act; nullptr when it cannot help.
+const int* support_table(dyson_ctx* c, int ncol) {
+  const int NT = (ncol + TC_TILE_COLS - 1) / TC_TILE_COLS;
+  std::vector<int> act((size_t)c->Nr * NT, std::numeric_limits<int>::max());
+  int far = 0;
+  for (int t = 0; t < NT; ++t) {
+    const int v1 = std::min(ncol, (t + 1) * TC_TILE_COLS);
+    int last = -1;
+    for (int v = t * TC_TILE_COLS; v < v1; ++v) {
+      const int s = c->h_src_site[v];
+      if (s == last) continue;
+      last = s;
+      const int sx = s % c->Lx, sy = s / c->Lx;
+      for (int i = 0; i < c->Nr; ++i) {
+        const int d = std::abs(i % c->Lx - sx) + std::abs(i / c->Lx - sy);
+        int& a = act[(size_t)i * NT + t];
+        a = std::min(a, d);
+      }
+    }
+  }
+  for (int a : act) far = std::max(far, a);
+  if (far < 2) return nullptr;                           // every tile is live from the first sweeps
+  const size_t bytes = act.size() * sizeof(int);
+  if (c->act_bytes < bytes) {
+    if (c->d_act) cudaFree(c->d_act);
+    c->d_act = nullptr;
+    c->act_bytes = 0;
+    if (cudaMalloc(&c->d_act, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;                                    // optional: run untruncated
+    }
+    c->act_bytes = bytes;
+  }
+  // pageable source: the copy completes before the call returns
+  if (cudaMemcpyAsync(c->d_act, act.data(), bytes, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return c->d_act;
+}
+
 // complex FP32 series refined by FP64 residuals: G += solve(r), r = B + K G - G
 int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int max_sweeps, double2** result,
                 dyson_report* rep) {
@@ -301,8 +350,12 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
       rep->inner_gmres = 1;
     } else {
       double peak = 0.0;
+      // the first right-hand side lives on the source sites: truncate its sweeps
+      const int* act = ref == 0 && c->support_trunc && c->use_tc && precision == DYSON_PREC_TF32X3_F64REF
+                           ? support_table(c, ncol)
+                           : nullptr;
       rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep, &peak,
-                       may_switch ? kSeriesPeakMax : std::numeric_limits<double>::infinity());
+                       may_switch ? kSeriesPeakMax : std::numeric_limits<double>::infinity(), act);
       if (rc == DYSON_ERR_DIVERGED && may_switch) {
         gmres = true;                                    // redo this refinement with GMRES
         --ref;
@@ -858,6 +911,12 @@ int dyson_set_inner_solver(dyson_ctx* c, int solver, int32_t restart) {
   return DYSON_OK;
 }
 
+int dyson_set_support_truncation(dyson_ctx* c, int enable) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  c->support_trunc = enable != 0;
+  return DYSON_OK;
+}
+
 int dyson_set_sweep_variant(dyson_ctx* c, int variant) {
   if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
   if (variant != DYSON_SWEEP_SINGLE_CTA && variant != DYSON_SWEEP_CTA_PAIR)
@@ -877,7 +936,7 @@ void dyson_destroy(dyson_ctx* c) {
   if (c->d_sym_perm) cudaFree(c->d_sym_perm);
   void* ptrs[] = {c->dU, c->dJ, c->d_nbr, c->d_nbond, c->d_eps, c->d_phase, c->d_lam, c->d_JW, c->d_Jz,
                   c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_src_site, c->d_src_time,
-                  c->d_norm, c->adj};
+                  c->d_norm, c->adj, c->d_act};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_norm) cudaFreeHost(c->h_norm);

@@ -142,6 +142,9 @@ struct dyson_ctx {
   int* d_sym_perm = nullptr;         // [8][Nr]: site j <- g^{-1}(j) for each operation g
   int inner_solver = 2;              // DYSON_INNER_SERIES, DYSON_INNER_GMRES or DYSON_INNER_AUTO
   int gmres_restart = 40;            // restart length (capped by free memory)
+  bool support_trunc = true;         // skip tiles outside the first series' support (dyson_set_support_truncation)
+  int* d_act = nullptr;              // [Nr][column tiles] first live sweep per tile
+  size_t act_bytes = 0;
   bool oz_enabled = true;            // DYSON_NO_OZ=1 keeps the FP64 CUDA-core residual
   bool use_oz = false;               // chosen for the current solve
 

@@ -37,6 +37,7 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, BK = 32, STAGES = 2;
+static_assert(BN == TC_TILE_COLS, "support-truncation tables are laid out per GEMM column tile");
 constexpr int PREFETCH = 4;                            // k-blocks of L2 prefetch ahead of the loads
 constexpr int A_TILE = BM * BK * 4;                    // 16 KB
 constexpr int X_TILE = BN * BK * 4;                    // 32 KB
@@ -110,11 +111,15 @@ __device__ __forceinline__ int find_inst(const TcInst* __restrict__ tab, int n, 
 __device__ __forceinline__ bool inst_active(const TcInst& I) { return I.active == nullptr || *I.active != 0; }
 
 // single instance: pointers and sizes as kernel parameters (32 registers, 8 blocks per SM)
+// act (optional, [Nr][column tiles of BN]): the first sweep at which the tile can
+// be non-zero; blocks of later tiles are skipped (support truncation)
 __global__ __launch_bounds__(256) void k_tc_gather_one(const float* __restrict__ din, const float* __restrict__ Jz,
                                                        const int* __restrict__ nbr, const int* __restrict__ nbond,
-                                                       float* __restrict__ X, int Nr, int Nc, int ncol) {
+                                                       float* __restrict__ X, int Nr, int Nc, int ncol,
+                                                       const int* __restrict__ act, int sweep) {
   const int i = blockIdx.x % Nr;
   const int nblk = blockIdx.x / Nr;
+  if (act && act[i * ((ncol + BN - 1) / BN) + (nblk * GATHER_COLS) / BN] > sweep) return;
   const int N2 = 2 * Nc;
   int nb[4], bd[4];
 #pragma unroll
@@ -271,7 +276,10 @@ struct TileRef {
   bool active;
 };
 
-__device__ __forceinline__ TileRef decode_tile(const TcInst* __restrict__ tab, int ninst, int tile) {
+// act/sweep: support truncation of a one-entry table (tiles whose act entry exceeds
+// the sweep hold zeros and are skipped), act == nullptr: none
+__device__ __forceinline__ TileRef decode_tile(const TcInst* __restrict__ tab, int ninst, int tile,
+                                               const int* __restrict__ act, int sweep) {
   TileRef T;
   T.k = find_inst<0>(tab, ninst, tile);
   T.I = &tab[T.k];
@@ -282,14 +290,14 @@ __device__ __forceinline__ TileRef decode_tile(const TcInst* __restrict__ tab, i
   T.mt = lt % MT;
   T.nt = (lt / MT) % NT;
   T.site = lt / (MT * NT);
-  T.active = inst_active(*T.I);
+  T.active = inst_active(*T.I) && !(act && act[T.site * NT + T.nt] > sweep);
   return T;
 }
 
 template <int MAXI>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ TcMaps<MAXI> maps, const TcInst* __restrict__ tab, int ninst, int tiles,
-              int parity, int* __restrict__ err) {
+              int parity, int* __restrict__ err, const int* __restrict__ act, int sweep) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -328,7 +336,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int g = 0;                                        // k-blocks issued by this CTA
       bool ok = true;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const TileRef T = decode_tile(tab, ninst, tile);
+        const TileRef T = decode_tile(tab, ninst, tile, act, sweep);
         if (!T.active) continue;
         const CUtensorMap* ma_hi = &maps.a_hi[T.k];
         const CUtensorMap* ma_lo = &maps.a_lo[T.k];
@@ -338,7 +346,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         TileRef N;
         N.active = false;
         for (; t2 < tiles; t2 += gridDim.x) {
-          N = decode_tile(tab, ninst, t2);
+          N = decode_tile(tab, ninst, t2, act, sweep);
           if (N.active) break;
         }
         for (int kb = 0; kb < T.KB; ++kb, ++g) {
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int g = 0, t = 0;
       bool ok = true, any = false;
       for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-        const TileRef T = decode_tile(tab, ninst, tile);
+        const TileRef T = decode_tile(tab, ninst, tile, act, sweep);
         if (!T.active) continue;
         const int buf = t & 1;
         if (t >= 2 && !mbar_wait(&acc_empty[buf], ((t >> 1) - 1) & 1, abort_p)) break;
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     int g = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-      const TileRef T = decode_tile(tab, ninst, tile);
+      const TileRef T = decode_tile(tab, ninst, tile, act, sweep);
       if (!T.active) continue;
       for (int kb = 0; kb < T.KB; ++kb, ++g) {
         const int s = g % STAGES;
@@ -438,7 +446,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q4 = warp - 8;                            // TMEM lane quarter (warp % 4)
     int t = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-      const TileRef T = decode_tile(tab, ninst, tile);
+      const TileRef T = decode_tile(tab, ninst, tile, act, sweep);
       if (!T.active) continue;
       const int buf = t & 1;
       bool go = mbar_wait(&acc_full[buf], (t >> 1) & 1, abort_p);
@@ -817,7 +825,8 @@ namespace {
 
 template <int MAXI>
 int launch_gemm(dyson_ctx* c, const CUtensorMap* a_hi, const CUtensorMap* a_lo, const CUtensorMap* x,
-                const TcInst* d_tab, int ninst, int tiles, int parity, cudaStream_t stream) {
+                const TcInst* d_tab, int ninst, int tiles, int parity, cudaStream_t stream, const int* act,
+                int sweep) {
   TcState* st = state(c);
   static_assert(sizeof(TcMaps<MAXI>) <= 30000, "tensor maps exceed the kernel-parameter space");
   TcMaps<MAXI> maps;
@@ -827,7 +836,8 @@ int launch_gemm(dyson_ctx* c, const CUtensorMap* a_hi, const CUtensorMap* a_lo, 
     maps.x[k] = x[k];
   }
   const int grid = std::min(tiles, st->num_sms > 0 ? st->num_sms : 148);
-  k_tc_gemm<MAXI><<<grid, THREADS, SMEM_BYTES, stream>>>(maps, d_tab, ninst, tiles, parity, st->d_err);
+  k_tc_gemm<MAXI><<<grid, THREADS, SMEM_BYTES, stream>>>(maps, d_tab, ninst, tiles, parity, st->d_err, act,
+                                                         sweep);
   return DYSON_OK;
 }
 
@@ -835,22 +845,25 @@ int launch_gemm(dyson_ctx* c, const CUtensorMap* a_hi, const CUtensorMap* a_lo, 
 
 int tc_launch_table(dyson_ctx* c, const TcInst* d_tab, int ninst, int tiles, int gblocks, int parity, int phases,
                     cudaStream_t stream, const CUtensorMap* a_hi, const CUtensorMap* a_lo, const CUtensorMap* x,
-                    const TcInst* h_one) {
+                    const TcInst* h_one, const int* act, int sweep) {
   if (ninst < 1 || ninst > TC_MAX_INSTANCES)
     return ctx_fail(c, DYSON_ERR_INVALID_ARG, "instance table of 1.." + std::to_string(TC_MAX_INSTANCES) + " entries");
+  if (act && !(ninst == 1 && h_one))
+    return ctx_fail(c, DYSON_ERR_INVALID_ARG, "support truncation needs a one-entry table with its host copy");
   TcState* st = state(c);
   if (phases & TC_GATHER) {
     if (h_one && ninst == 1)
       k_tc_gather_one<<<gblocks, 256, 0, stream>>>(h_one->buf[parity], h_one->Jz, h_one->nbr, h_one->nbond, h_one->X,
-                                                   h_one->Nr, h_one->Nc, h_one->ncol);
+                                                   h_one->Nr, h_one->Nc, h_one->ncol, act, sweep);
     else
       k_tc_gather<<<gblocks, 256, 0, stream>>>(d_tab, ninst, parity);
     DY_CUDA(c, cudaGetLastError());
     c->launches += 1;
   }
   if (phases & TC_GEMM) {
-    int rc = ninst == 1 ? launch_gemm<1>(c, a_hi, a_lo, x, d_tab, ninst, tiles, parity, stream)
-                        : launch_gemm<TC_MAX_INSTANCES>(c, a_hi, a_lo, x, d_tab, ninst, tiles, parity, stream);
+    int rc = ninst == 1 ? launch_gemm<1>(c, a_hi, a_lo, x, d_tab, ninst, tiles, parity, stream, act, sweep)
+                        : launch_gemm<TC_MAX_INSTANCES>(c, a_hi, a_lo, x, d_tab, ninst, tiles, parity, stream,
+                                                        nullptr, 0);
     if (rc) return rc;
     DY_CUDA(c, cudaGetLastError());
     c->launches += 1;
@@ -858,12 +871,14 @@ int tc_launch_table(dyson_ctx* c, const TcInst* d_tab, int ninst, int tiles, int
   return DYSON_OK;
 }
 
-int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, int phases) {
+int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, int phases,
+             const int* act, int sweep) {
   int rc = tc_prepare(c, ncol);
   if (rc) return rc;
   TcState* st = state(c);
   const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;
-  if (!(phases & TC_TABLE_ONLY) && tc_uses_pair(c)) {
+  // truncated sweeps run on the single-CTA kernel, which skips tiles
+  if (!(phases & TC_TABLE_ONLY) && !act && tc_uses_pair(c)) {
     if (phases & TC_GATHER) {
       // the one-entry table serves the gather of the pair form too
       if ((rc = tc_sweep(c, ncol, gs, r, din, dout, TC_GATHER | TC_TABLE_ONLY))) return rc;
@@ -918,7 +933,7 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
     parity = 0;
   }
   return tc_launch_table(c, st->d_inst, 1, tc_instance_tiles(*h), tc_instance_gather_blocks(*h), parity,
-                         phases & (TC_GATHER | TC_GEMM), c->stream, &st->a_hi, &st->a_lo, &st->x, h);
+                         phases & (TC_GATHER | TC_GEMM), c->stream, &st->a_hi, &st->a_lo, &st->x, h, act, sweep);
 }
 
 int tc_check_error(dyson_ctx* c) {

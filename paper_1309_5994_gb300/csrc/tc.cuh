@@ -39,9 +39,14 @@ bool tc_uses_pair(dyson_ctx* c);
 // one sweep d_out = r + K d_in over the FP32 planar chunk state of ncol vector columns;
 // writes c->d_norm[q] for groups of gs columns (gs a multiple of 32, Nc a multiple of 64).
 // phases: TC_GATHER launches X = J d_in, TC_GEMM launches the tensor-core product and
-// epilogue (in that order; both = one whole sweep)
+// epilogue (in that order; both = one whole sweep).
+// act (optional, device [Nr][ceil(ncol / 256)]): support truncation (App. C, Sec. IV.D):
+// the first sweep at which each (site, 256-column tile) can be non-zero; tiles with
+// act > sweep are skipped, so their d_out must already hold zeros.
 enum { TC_GATHER = 1, TC_GEMM = 2, TC_TABLE_ONLY = 4 };
-int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* d_in, float* d_out, int phases);
+constexpr int TC_TILE_COLS = 256;
+int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* d_in, float* d_out, int phases,
+             const int* act = nullptr, int sweep = 0);
 // DYSON_ERR_TIMEOUT if a bounded pipeline wait of an earlier sweep expired (clears the flag)
 int tc_check_error(dyson_ctx* c);
 // free tensor-core module state
@@ -62,4 +67,4 @@ int tc_instance_gather_blocks(const TcInst& e);   // gather blocks of the entry
 // gather then takes the entry's pointers as kernel parameters), else nullptr.
 int tc_launch_table(dyson_ctx* c, const TcInst* d_tab, int ninst, int tiles, int gblocks, int parity, int phases,
                     cudaStream_t stream, const CUtensorMap* a_hi, const CUtensorMap* a_lo, const CUtensorMap* x,
-                    const TcInst* h_one = nullptr);
+                    const TcInst* h_one = nullptr, const int* act = nullptr, int sweep = 0);

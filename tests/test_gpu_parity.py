@@ -115,11 +115,44 @@ def test_pair_kernel_ragged_column_tiles(torch_cuda, lib):
     ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
     s = _solver(p)
     s.set_sweep_variant(1)
+    s.set_support_truncation(False)          # truncated sweeps would run on the single-CTA kernel
     s.profile(True)
     got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
     assert s.profile_query(5)[0] > 0 and s.profile_query(2)[0] == 0
     for q, i in enumerate(sources):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["nc64_ragged", "nc256_pair"])
+def test_support_truncation_is_bit_identical(torch_cuda, lib, case):
+    """Skipping the (site, column-tile) blocks the first series has not reached yet
+    changes no bit of the result and no sweep count; both agree with the dense solve.
+    Nc = 64: five block columns in two 256-column tiles (the second ragged), four
+    sources sharing a tile.  Nc = 256 with the CTA-pair variant: the truncated first
+    series runs on the single-CTA kernel, the later refinements on the pair."""
+    if case == "nc64_ragged":
+        kw, sources, variant = dict(L=6, Ly=5, Nt=24, Nm=16, trap_c=0.1, U0=20.0), [0, 7, 29, 13, 22], 0
+    else:
+        kw, sources, variant = dict(L=4, Ly=3, Nt=96, Nm=64, trap_c=0.1, U0=20.0), [0, 11], 1
+    p = wl.random_tables(wl.small(**kw), seed=13, rel=0.2)
+    out = {}
+    for trunc in (True, False):
+        s = _solver(p)
+        s.set_sweep_variant(variant)
+        s.set_support_truncation(trunc)
+        s.profile(True)
+        out[trunc] = _solve(torch_cuda, s, p, sources, 1, tol=1e-13) + (
+            s.profile_query(2)[0], s.profile_query(5)[0])
+        s.close()
+    (g1, r1, single1, pair1), (g0, r0, single0, pair0) = out[True], out[False]
+    assert np.array_equal(g1, g0)
+    assert r1.report["sweeps"] == r0.report["sweeps"] and r1.report["refinements"] == r0.report["refinements"]
+    if variant == 1:
+        assert single1 > 0 and pair1 > 0 and single0 == 0
+    S = dyson.setup(p)
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    for q in range(len(sources)):
+        assert _rel(g1[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
 
 def test_c4v_wedge_solve_equals_the_full_solve(torch_cuda, lib):
