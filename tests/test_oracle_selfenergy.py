@@ -1,0 +1,126 @@
+"""Pins of the oracle's self-energy step (Sec. III, Eqs. (selfcons)-(defnSigmatilde)) against
+facts fixed by the many-body definitions: the closed-form two-point function, Wick's theorem,
+exchange antisymmetry, equal-point values and the local Dyson equation."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import atomic, contour, dyson
+from oracle import selfenergy as se
+
+
+@pytest.fixture(scope="module")
+def grid():
+    c = contour.make_contour(4, 3, 0.11, 1.3)
+    U_t = 7.0 * (1.0 + 0.2 * np.sin(5.0 * np.arange(4) * 0.11))
+    return c, U_t
+
+
+def test_two_point_function_equals_the_closed_form(grid):
+    """The Fock-space machinery that builds the two-particle function reproduces Lambda of Sec. III
+    (itself pinned to a separate trace over T_C-ordered products)."""
+    c, U_t = grid
+    for eps in (-3.5, 0.7):
+        assert np.abs(se.two_point(c, eps, U_t) - atomic.atomic_gf(c, eps, U_t, c.beta)).max() < 1e-13
+
+
+@pytest.mark.parametrize("eps", [-1.3, 0.4])
+def test_cumulant_vanishes_without_interaction(grid, eps):
+    """U = 0: the site is non-interacting, Wick's theorem holds for every contour ordering
+    (coincident points included), so the cumulant of both spin channels is zero."""
+    c, _ = grid
+    for same in (True, False):
+        G0 = se.two_point(c, eps, np.zeros(c.Nt))
+        G2 = se.two_particle(c, eps, np.zeros(c.Nt), same)
+        wick = -np.einsum("ac,bd->abcd", G0, G0) * (1.0 if same else 0.0) + np.einsum("ad,bc->abcd", G0, G0)
+        assert np.abs(G2 - wick).max() < 1e-14
+    assert np.abs(se.cumulant_sum(c, eps, np.zeros(c.Nt))).max() < 1e-14
+
+
+def test_cumulant_is_nonzero_with_interaction(grid):
+    c, U_t = grid
+    assert np.abs(se.cumulant_sum(c, -3.5, U_t)).max() > 0.05
+
+
+def test_exchange_antisymmetry(grid):
+    """Same spins: swapping the two annihilators or the two creators flips the sign."""
+    c, U_t = grid
+    G2 = se.two_particle(c, -3.5, U_t, True)
+    assert np.abs(G2 + np.transpose(G2, (1, 0, 2, 3))).max() < 1e-15
+    assert np.abs(G2 + np.transpose(G2, (0, 1, 3, 2))).max() < 1e-15
+    # opposite spins: swapping both pairs at once exchanges the roles of the two spins,
+    # which the paramagnetic site leaves unchanged
+    G2o = se.two_particle(c, -3.5, U_t, False)
+    assert np.abs(G2o - np.transpose(G2o, (1, 0, 3, 2))).max() < 1e-13
+
+
+def test_equal_point_values_are_the_atomic_occupations(grid):
+    """All four operators at one point: on the forward and imaginary branches the creators are
+    later, the product is n_up n_dn and G2_{up dn} = (-i)^2 rho_d; on the backward branch the
+    annihilators are later, the product is (1 - n_up)(1 - n_dn) and G2 = (-i)^2 rho_0."""
+    c, U_t = grid
+    eps = -2.9
+    G2o = se.two_particle(c, eps, U_t, False)
+    lr0, _, lrd = atomic.boltzmann_log_weights(eps, U_t[0], c.beta)
+    for z in range(c.Nc):
+        want = -np.exp(lr0) if c.branch[z] == contour.BWD else -np.exp(lrd)
+        assert abs(G2o[z, z, z, z] - want) < 1e-14
+
+
+def test_turning_point_makes_the_atomic_matrix_singular():
+    """The last forward and the first backward point carry the same time, and by the equal-point
+    rule G0 has equal columns there: rank Nc - 1, every other singular value O(1)."""
+    p = wl.small(L=2, Ly=1, Nt=5, Nm=4, dt=0.1, aU=0.1, aJ=0.2, omega=5.0)
+    S = dyson.setup(p)
+    G0 = S.Lam[0]
+    Nt = p.Nt
+    assert np.array_equal(G0[:, Nt - 1], G0[:, Nt])
+    sv = np.linalg.svd(G0, compute_uv=False)
+    assert sv[-1] < 1e-14 * sv[0] and sv[-2] > 0.1
+
+
+def test_local_block_solves_the_local_dyson_equation():
+    """B = (I - G0 T)^-1 G0 satisfies B = G0 + G0 W Sigma W B with W Sigma W = T = G0^+ Sigma~ G0^+,
+    and for an invertible G0 it is G0 (G0 - Sigma~)^-1 G0."""
+    p = wl.small(L=2, Ly=1, Nt=5, Nm=4, dt=0.1, aU=0.1, aJ=0.2, omega=5.0)
+    S = dyson.setup(p)
+    rng = np.random.default_rng(4)
+    G0 = S.Lam[0]
+    St = 0.05 * (rng.normal(size=G0.shape) + 1j * rng.normal(size=G0.shape))
+    T = se.weighted_sigma(G0, St)
+    B = se.local_block(G0, T)
+    Sig = se.sigma_contour(S, G0, St)
+    W = S.contour.W
+    assert np.abs(B - G0 - G0 @ (W[:, None] * Sig * W[None, :]) @ B).max() < 1e-12 * np.abs(B).max()
+    A = G0 + 0.3 * np.eye(G0.shape[0])                     # invertible: the plain-inverse form
+    Ba = se.local_block(A, se.weighted_sigma(A, St))
+    assert np.abs(Ba - A @ np.linalg.solve(A - St, A)).max() < 1e-11 * np.abs(Ba).max()
+
+
+def test_sigma_tilde_vanishes_at_zero_hopping_and_scales_as_J_squared():
+    """Sigma~ carries the hopping twice (Eq. (defnSigmatilde)): zero at J = 0, x4 when J doubles
+    (for a fixed Gloc)."""
+    p = wl.small(L=2, Ly=2, Nt=4, Nm=3, dt=0.1, U0=6.0, J0=0.3)
+    S = dyson.setup(p)
+    K = se.cumulant_sum(S.contour, S.eps[0], S.U[0], S.Lam[0])
+    Gloc = S.Lam
+    s1 = se.sigma_tilde(S, K, Gloc, 0)
+    S.Jz = 2.0 * S.Jz
+    s2 = se.sigma_tilde(S, K, Gloc, 0)
+    assert np.abs(s2 - 4.0 * s1).max() < 1e-13 * np.abs(s2).max()
+    S.Jz = 0.0 * S.Jz
+    assert np.abs(se.sigma_tilde(S, K, Gloc, 0)).max() == 0.0
+
+
+def test_self_consistency_converges_to_a_fixed_point():
+    """The loop of Sec. IV.C reaches the criterion, and its result reproduces itself."""
+    p = wl.small(L=2, Ly=2, Nt=4, Nm=3, dt=0.1, U0=8.0, J0=0.5, trap_c=0.2, aU=0.1, aJ=0.2, omega=5.0)
+    blocks, St, Gloc, its, hist = se.self_consistent(p, mix=0.7, delta_sc=1e-10, max_iter=60)
+    assert hist[-1] <= 1e-10 and its < 60
+    S = dyson.setup(p)
+    G2 = se.local_greens(S, blocks)
+    St2 = np.stack([se.sigma_tilde(S, se.cumulant_sum(S.contour, S.eps[i], S.U[i], S.Lam[i]), G2, i)
+                    for i in range(S.Nr)])
+    assert np.abs(St2 - St).max() < 1e-8 * np.abs(St).max()
+    # and it differs from the first-order (Sigma = 0) lattice function
+    assert np.abs(G2 - se.local_greens(S, S.Lam)).max() > 1e-4
