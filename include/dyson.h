@@ -194,6 +194,39 @@ int dyson_adjoint_obs(dyson_ctx* ctx, const double* w_density, const double* w_d
  * on_device != 0 means the pointers are device memory, else host memory. */
 int dyson_observables(dyson_ctx* ctx, double* n, double* ekin, double* docc, int on_device);
 
+/* Local Green's functions: solves the block columns of the sites src[0..n_src)
+ * as dyson_solve_columns does (same precision, tolerance, report and codes;
+ * observables are recorded too) and writes only their diagonal blocks,
+ * gloc[s][z][z'] = G_ss(z, z'), DEVICE memory [Nr][Nc][Nc] complex128 (rows of
+ * sites not in src are left untouched).  The symmetry setting is not used.  The
+ * input of the self-energy step below. */
+int dyson_local_greens(dyson_ctx* ctx, const int32_t* src_sites, int64_t n_src, int precision, double tol,
+                       int32_t max_sweeps, double* gloc, dyson_report* rep);
+
+/* Self-energy step of the strong-coupling expansion (Sec. III, Eqs. (selfcons),
+ * (defnSigma), (defnSigmatilde); Sec. IV.C, Eq. (Sigmamix)).  From the local
+ * Green's functions gloc of every site (DEVICE [Nr][Nc][Nc] complex128, e.g. from
+ * dyson_local_greens over all sites):
+ *   Sigma~_i(a, d) = - sum_{j in NN(i)} sum_{b, c} K_i(a, b; c, d) W_c J_ij(c) Gloc_j(c, b) J_ji(b) W_b,
+ * K_i the second-order cumulant of the isolated site i summed over the
+ * neighbour's spin, evaluated on the fly from the site's phases (O(Nc^4) per
+ * site, FP64); then Sigma_i = W^-1 G0_i^+ Sigma~_i G0_i^+ W^-1 (G0 = the atomic
+ * Lambda of the last dyson_build_sigma; the contour inverse is read with the
+ * pseudo-inverse because the turning point of the discretised contour makes G0
+ * singular), mixed as Sigma = mix Sigma_new + (1 - mix) Sigma_old (Sigma_old = 0
+ * after dyson_build_sigma), and the local block
+ *   B_i = (I - G0_i W Sigma_i W)^-1 G0_i
+ * replaces Lambda_i for the following solves (all precisions).
+ *   sigma_tilde  DEVICE [Nr][Nc][Nc] complex128 or NULL: receives Sigma~_new;
+ *   criterion    host or NULL: N_bd^-1 |Sigma_new - Sigma_old|_F + |Sigma_new - Sigma_old|_max
+ *                (N_bd = Nr Nc^2 block-diagonal entries), the paper's convergence measure.
+ * dyson_build_sigma returns to Sigma = 0.  Device memory: 8 Nr Nc^2 complex128.
+ * Returns INVALID_ARG for mix outside (0, 1] or a NULL gloc, STATE before
+ * dyson_build_sigma or with Lambda transposed, DIVERGED if a local system is
+ * singular.  dyson_adjoint and dyson_adjoint_obs return STATE while a local block
+ * is installed (they differentiate the atomic Lambda). */
+int dyson_selfenergy_step(dyson_ctx* ctx, const double* gloc, double mix, double* sigma_tilde, double* criterion);
+
 /* Delta t -> 0 extrapolation (Sec. IV.D).  The same tables computed on n_grids
  * contours whose steps are h_b = h_0 / m_b (integer divisors, m_0 = 1 < m_1 <
  * ...; the real-time grid of contour b has at least m_b (nt[0] - 1) + 1

@@ -73,7 +73,8 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
            "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune", "dyson_set_symmetry",
-           "dyson_adjoint_obs", "dyson_extrapolate_dt", "dyson_set_support_truncation"]
+           "dyson_adjoint_obs", "dyson_extrapolate_dt", "dyson_set_support_truncation", "dyson_local_greens",
+           "dyson_selfenergy_step"]
 SYMMETRY_NONE, SYMMETRY_C4V = 0, 1
 INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
@@ -109,6 +110,9 @@ def load(path: str = _LIB_PATH):
     lib.dyson_autotune.argtypes = [P, C.c_int32, C.POINTER(Tuning)]
     lib.dyson_set_symmetry.argtypes = [P, C.c_int]
     lib.dyson_set_support_truncation.argtypes = [P, C.c_int]
+    lib.dyson_local_greens.argtypes = [P, C.POINTER(C.c_int32), C.c_int64, C.c_int, C.c_double, C.c_int32, P,
+                                       C.POINTER(Report)]
+    lib.dyson_selfenergy_step.argtypes = [P, P, C.c_double, P, C.POINTER(C.c_double)]
     lib.dyson_launch_count.argtypes = [P]
     lib.dyson_launch_count.restype = C.c_int64
     lib.dyson_solve_block_column_noalloc.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
@@ -310,6 +314,30 @@ class Solver:
 
     def set_inner_solver(self, solver: int, restart: int = 0):
         self._check(self.lib.dyson_set_inner_solver(self.h, solver, restart))
+
+    def local_greens(self, sources=None, precision=PREC_F64, tol=1e-13, max_sweeps=400, out=None, allow=(0,)):
+        """Diagonal blocks G_ss of the block columns `sources` (default: every site) into
+        `out`, a complex128 device tensor [Nr, Nc, Nc] (allocated when None).  Returns (out, SolveResult)."""
+        torch = self._torch
+        src = np.ascontiguousarray(np.asarray(range(self.p.Nr) if sources is None else sources, dtype=np.int32))
+        if out is None:
+            out = torch.zeros((self.p.Nr, self.p.Nc, self.p.Nc), dtype=torch.complex128,
+                              device=torch.device("cuda", self.device))
+        assert out.is_cuda and out.dtype == torch.complex128 and out.is_contiguous()
+        assert out.numel() == self.p.Nr * self.p.Nc * self.p.Nc
+        rep = Report()
+        rc = self.lib.dyson_local_greens(self.h, src.ctypes.data_as(C.POINTER(C.c_int32)), len(src), precision, tol,
+                                         max_sweeps, C.c_void_p(out.data_ptr()), C.byref(rep))
+        self._check(rc, ok=allow)
+        return out, SolveResult(rc, rep.as_dict())
+
+    def selfenergy_step(self, gloc, mix=0.7, sigma_tilde=None):
+        """One self-energy step from the local Green's functions `gloc` (device [Nr, Nc, Nc]);
+        installs the new local blocks and returns the convergence measure."""
+        crit = C.c_double()
+        st = C.c_void_p(sigma_tilde.data_ptr()) if sigma_tilde is not None else None
+        self._check(self.lib.dyson_selfenergy_step(self.h, C.c_void_p(gloc.data_ptr()), mix, st, C.byref(crit)))
+        return crit.value
 
     def set_support_truncation(self, enable: bool):
         self._check(self.lib.dyson_set_support_truncation(self.h, 1 if enable else 0))

@@ -524,6 +524,7 @@ int dyson_build_sigma(dyson_ctx* c) {
   c->sigma_built = true;
   c->lam32_built = c->lam_split_built = false;
   oz_invalidate(c);
+  se_invalidate(c);                                      // Sigma = 0: Lambda is the atomic G0 again
   return DYSON_OK;
 }
 
@@ -631,11 +632,11 @@ int fold_status(int status, int st) {
 
 extern "C" {
 
-int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
-                        int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
-  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
-  if (c->symmetry == DYSON_SYMMETRY_C4V)
-    return solve_columns_c4v(c, src, n_src, precision, tol, max_sweeps, g_out, rep_out);
+namespace {
+
+// block-column solves; g_out: full block columns, gloc: diagonal blocks G_ss at row s (either may be NULL)
+int solve_columns_impl(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
+                       int32_t max_sweeps, double* g_out, double* gloc, dyson_report* rep_out) {
   ReportScope R(c, rep_out);
   int rc = check_solve_args(c, precision, tol, max_sweeps);
   if (rc) return R.finish(rc);
@@ -677,6 +678,10 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
       launch_export(G, c->Nr, c->Nc, nq, (double2*)g_out + (size_t)start * c->Nr * c->Nc * c->Nc, c->stream);
       c->launches += 1;
     }
+    if (gloc) {
+      launch_export_diagonal(G, c->d_src_site, c->Nc, ncol, nq, (double2*)gloc, c->stream);
+      c->launches += 1;
+    }
     DY_CUDA(c, cudaGetLastError());
   }
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -684,6 +689,23 @@ int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int pre
   if (status == DYSON_ERR_NOT_CONVERGED) ctx_fail(c, status, "max_sweeps or refinement limit reached above tolerance");
   if (status == DYSON_ERR_DIVERGED) ctx_fail(c, status, "series diverged (update not finite or past the rounding limit, or refinement residual growing)");
   return R.finish(status);
+}
+
+}  // namespace
+
+int dyson_solve_columns(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
+                        int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (c->symmetry == DYSON_SYMMETRY_C4V)
+    return solve_columns_c4v(c, src, n_src, precision, tol, max_sweeps, g_out, rep_out);
+  return solve_columns_impl(c, src, n_src, precision, tol, max_sweeps, g_out, nullptr, rep_out);
+}
+
+int dyson_local_greens(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
+                       int32_t max_sweeps, double* gloc, dyson_report* rep_out) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (!gloc) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "gloc is NULL");
+  return solve_columns_impl(c, src, n_src, precision, tol, max_sweeps, nullptr, gloc, rep_out);
 }
 
 int dyson_solve_vector_columns(dyson_ctx* c, const int32_t* sites, const int32_t* times, int64_t n, int precision,
@@ -742,6 +764,8 @@ int dyson_adjoint_obs(dyson_ctx* c, const double* w_density, const double* w_doc
   int rc = check_solve_args(c, precision, tol, max_sweeps);
   if (rc) return R.finish(rc);
   if (c->sigma_transposed) return R.finish(ctx_fail(c, DYSON_ERR_STATE, "Lambda is transposed"));
+  if (c->se_installed)
+    return R.finish(ctx_fail(c, DYSON_ERR_STATE, "the adjoint differentiates the atomic Lambda: rebuild it first"));
   if ((!w_density && !w_docc) || t_index < 0 || t_index >= c->Nt || (w_docc && t_index < 1))
     return R.finish(ctx_fail(c, DYSON_ERR_INVALID_ARG, "need weights, 0 <= t_index < Nt (>= 1 with D weights)"));
   DeviceGuard g(c->device);
@@ -933,6 +957,7 @@ void dyson_destroy(dyson_ctx* c) {
   tc_release(c);
   oz_release(c);
   gmres_release(c);
+  se_release(c);
   if (c->d_sym_perm) cudaFree(c->d_sym_perm);
   void* ptrs[] = {c->dU, c->dJ, c->d_nbr, c->d_nbond, c->d_eps, c->d_phase, c->d_lam, c->d_JW, c->d_Jz,
                   c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_src_site, c->d_src_time,

@@ -70,6 +70,12 @@ void launch_accumulate(double2* G, const float* d, int Nr, int Nc, int ncol, cud
 void launch_observables(const double2* G, const int* src_site, int nq, const int* nbr,
                         const int* nbond, const double* Jtab, const double* eps, const double* U,
                         int Nr, int Nt, int Nc, int ncol, double dt, double* obs, cudaStream_t s);
+// diagonal blocks of a chunk of block columns: out[s][z][z'] = G_ss(z, z') for each source s
+void launch_export_diagonal(const double2* G, const int* src_site, int Nc, int ncol, int nq, double2* out,
+                            cudaStream_t s);
+// self-energy state: forget G0 (after a new Lambda build), free
+void se_invalidate(dyson_ctx* c);
+void se_release(dyson_ctx* c);
 // [j][q*Nc+z'][z] -> user layout [q][j][z][z']
 void launch_export(const double2* G, int Nr, int Nc, int nq, double2* out, cudaStream_t s);
 
@@ -145,6 +151,8 @@ struct dyson_ctx {
   bool support_trunc = true;         // skip tiles outside the first series' support (dyson_set_support_truncation)
   int* d_act = nullptr;              // [Nr][column tiles] first live sweep per tile
   size_t act_bytes = 0;
+  void* se = nullptr;                // self-energy step state (atomic G0, its pseudo-inverse, mixed T)
+  bool se_installed = false;         // Lambda holds the local block of a self-energy step
   bool oz_enabled = true;            // DYSON_NO_OZ=1 keeps the FP64 CUDA-core residual
   bool use_oz = false;               // chosen for the current solve
 

@@ -1,0 +1,37 @@
+"""The self-consistency loop of Sec. IV.C on one context.
+
+Each iteration solves the block columns of every site with the current local
+blocks (dyson_local_greens, only the diagonal blocks G_jj are kept), takes a
+self-energy step from them (dyson_selfenergy_step: Eqs. (defnSigmatilde) and
+(defnSigma), mixing of Eq. (Sigmamix), new local blocks installed) and stops when
+the paper's measure N_bd^-1 |dSigma|_F + |dSigma|_max falls to delta_sc
+(default 1e-8 times the largest U, the paper's suggestion).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding
+
+
+def self_consistent(solver, mix=0.7, delta_sc=None, max_iter=40, precision=binding.PREC_F64, tol=1e-13,
+                    max_sweeps=400):
+    """Run the loop on a Solver whose Lambda has been built.  Returns a dict with the
+    iteration count, the history of the measure, whether it converged, the last
+    local Green's functions (device tensor [Nr, Nc, Nc]) and the solve reports."""
+    if delta_sc is None:
+        delta_sc = 1e-8 * float(np.abs(solver.p.U).max())
+    gloc = None
+    hist, reports = [], []
+    converged = False
+    it = 0
+    for it in range(1, max_iter + 1):
+        gloc, res = solver.local_greens(None, precision=precision, tol=tol, max_sweeps=max_sweeps, out=gloc)
+        reports.append(res.report)
+        crit = solver.selfenergy_step(gloc, mix)
+        hist.append(crit)
+        if crit <= delta_sc:
+            converged = True
+            break
+    return {"iterations": it, "history": hist, "converged": converged, "gloc": gloc, "reports": reports,
+            "delta_sc": delta_sc}

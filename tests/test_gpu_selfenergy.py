@@ -1,0 +1,124 @@
+"""Self-energy step (Sec. III, Eqs. (defnSigmatilde), (defnSigma); Sec. IV.C mixing loop) on the GPU
+against the oracle."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import dyson
+from oracle import selfenergy as se
+
+pytestmark = pytest.mark.gpu
+
+DRIVEN = dict(L=3, Ly=2, Nt=7, Nm=5, dt=0.1, beta=1.0, U0=10.0, J0=1.0, trap_c=0.3, aU=0.1, aJ=0.2, omega=6.0)
+SMALL = dict(L=2, Ly=2, Nt=4, Nm=3, dt=0.1, U0=8.0, J0=0.5, trap_c=0.2, aU=0.1, aJ=0.2, omega=5.0)
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _solver(p):
+    from paper_1309_5994_gb300 import binding
+    s = binding.Solver(p, device=0)
+    s.build_sigma()
+    return s
+
+
+def _random_gloc(p, seed):
+    rng = np.random.default_rng(seed)
+    shape = (p.Nr, p.Nc, p.Nc)
+    return 0.3 * (rng.normal(size=shape) + 1j * rng.normal(size=shape))
+
+
+@pytest.mark.parametrize("kw", [DRIVEN, SMALL, dict(L=2, Ly=1, Nt=3, Nm=2, dt=0.2, beta=2.0, U0=6.0, J0=1.0)])
+def test_sigma_tilde_and_local_block_match_the_oracle(torch_cuda, lib, kw):
+    torch = torch_cuda
+    p = wl.small(**kw)
+    S = dyson.setup(p)
+    gloc = _random_gloc(p, 5)
+    s = _solver(p)
+    out = torch.empty((p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda")
+    s.selfenergy_step(torch.from_numpy(gloc).cuda(), mix=1.0, sigma_tilde=out)
+    got = out.cpu().numpy()
+    lam = s.sigma()
+    for i in range(p.Nr):
+        K = se.cumulant_sum(S.contour, S.eps[i], S.U[i], S.Lam[i])
+        ref = se.sigma_tilde(S, K, gloc, i)
+        assert np.abs(got[i] - ref).max() <= 1e-12 * np.abs(ref).max(), i
+        B = se.local_block(S.Lam[i], se.weighted_sigma(S.Lam[i], ref))
+        assert np.abs(lam[i] - B).max() <= 1e-10 * np.abs(B).max(), i
+
+
+def test_sigma_tilde_vanishes_without_interaction(torch_cuda, lib):
+    """U = 0: the connected two-particle part equals its disconnected (Wick) parts, so the
+    contraction kernel and the GEMM terms cancel."""
+    torch = torch_cuda
+    p = wl.small(L=3, Ly=2, Nt=6, Nm=4, dt=0.1, U0=0.0, J0=1.0, trap_c=0.3)
+    S = dyson.setup(p)
+    gloc = _random_gloc(p, 6)
+    s = _solver(p)
+    out = torch.empty((p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda")
+    s.selfenergy_step(torch.from_numpy(gloc).cuda(), mix=1.0, sigma_tilde=out)
+    got = out.cpu().numpy()
+    for i in range(p.Nr):
+        F = se.hybridisation(S, gloc, i)
+        scale = np.abs(S.Lam[i] @ F @ S.Lam[i]).max()
+        assert np.abs(got[i]).max() <= 1e-13 * scale
+
+
+def test_self_consistent_loop_matches_the_oracle(torch_cuda, lib):
+    from paper_1309_5994_gb300.selfconsistency import self_consistent
+    p = wl.small(**SMALL)
+    blocks, St, Gloc, its, hist = se.self_consistent(p, mix=0.7, delta_sc=1e-10, max_iter=60)
+    s = _solver(p)
+    r = self_consistent(s, mix=0.7, delta_sc=1e-10, max_iter=60, precision=0, tol=1e-14)
+    assert r["converged"] and abs(r["iterations"] - its) <= 1
+    n = min(len(hist), len(r["history"]))
+    h0, h1 = np.array(hist[:n - 2]), np.array(r["history"][:n - 2])
+    assert np.all(np.abs(h1 - h0) <= 1e-6 * h0 + 1e-9)
+    g = r["gloc"].cpu().numpy()
+    assert np.abs(g - Gloc).max() <= 1e-9 * np.abs(Gloc).max()
+    assert np.abs(s.sigma() - blocks).max() <= 1e-9 * np.abs(blocks).max()
+
+
+def test_mixed_precision_loop_agrees_with_fp64(torch_cuda, lib):
+    """Nc = 64 (the tensor-core sweeps and the split-product residual run on the installed blocks)."""
+    from paper_1309_5994_gb300.selfconsistency import self_consistent
+    p = wl.small(L=3, Ly=3, Nt=24, Nm=16, dt=0.05, beta=2.0, U0=20.0, J0=1.0, trap_c=0.05, aU=0.1, aJ=0.2,
+                 omega=20.0)
+    out = {}
+    for prec, tol in ((0, 1e-13), (1, 1e-11)):
+        s = _solver(p)
+        s.profile(True)
+        out[prec] = self_consistent(s, mix=0.7, delta_sc=1e-7, max_iter=40, precision=prec, tol=tol)
+        if prec == 1:
+            assert s.profile_query(2)[0] > 0 and s.profile_query(4)[0] > 0
+        out[prec]["lam"] = s.sigma()
+        s.close()
+    assert out[0]["converged"] and out[1]["converged"]
+    g0, g1 = out[0]["gloc"].cpu().numpy(), out[1]["gloc"].cpu().numpy()
+    assert np.abs(g1 - g0).max() <= 1e-8 * np.abs(g0).max()
+    assert np.abs(out[1]["lam"] - out[0]["lam"]).max() <= 1e-8 * np.abs(out[0]["lam"]).max()
+
+
+def test_step_arguments_and_state(torch_cuda, lib):
+    from paper_1309_5994_gb300 import binding
+    torch = torch_cuda
+    p = wl.small(**SMALL)
+    s = binding.Solver(p, device=0)
+    g = torch.zeros((p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda")
+    with pytest.raises(binding.DysonError, match="STATE"):
+        s.selfenergy_step(g)                                  # Lambda not built
+    s.build_sigma()
+    with pytest.raises(binding.DysonError, match="INVALID_ARG"):
+        s.selfenergy_step(g, mix=0.0)
+    s.selfenergy_step(torch.from_numpy(_random_gloc(p, 1)).cuda(), mix=0.7)
+    with pytest.raises(binding.DysonError, match="STATE"):
+        s.adjoint(np.ones(p.Nr))                              # the adjoint differentiates the atomic Lambda
+    s.build_sigma()                                           # back to Sigma = 0
+    S = dyson.setup(p)
+    assert np.abs(s.sigma() - S.Lam).max() < 1e-13
