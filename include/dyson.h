@@ -263,7 +263,8 @@ enum {
   DYSON_KERNEL_RESIDUAL_SPLIT = 4,/* the same residual from BF16 slice products on tcgen05   */
   DYSON_KERNEL_SWEEP_TC_PAIR = 5, /* the same GEMM on CTA pairs (tcgen05 cta_group::2, M=256) */
   DYSON_KERNEL_GATHER_TC = 6,     /* neighbour gather X = J d of the tensor-core sweep        */
-  DYSON_KERNEL_KINDS = 7
+  DYSON_KERNEL_SELFENERGY = 7,    /* connected cumulant contraction of the self-energy step  */
+  DYSON_KERNEL_KINDS = 8
 };
 
 /* Enable (1) or disable (0) event timing of every sweep/residual launch on the

@@ -23,7 +23,7 @@ PREC_TF32X3_F64REF = 1
 KERNEL_SWEEP_F64, KERNEL_SWEEP_F32, KERNEL_SWEEP_TC, KERNEL_RESIDUAL_F64, KERNEL_RESIDUAL_SPLIT = 0, 1, 2, 3, 4
 KERNEL_SWEEP_TC_PAIR, KERNEL_GATHER_TC = 5, 6
 KERNEL_NAMES = {0: "sweep_f64", 1: "sweep_f32_simt", 2: "sweep_tc_3xtf32", 3: "residual_f64",
-                4: "residual_split_bf16", 5: "sweep_tc_3xtf32_pair", 6: "gather_tc"}
+                4: "residual_split_bf16", 5: "sweep_tc_3xtf32_pair", 6: "gather_tc", 7: "selfenergy_conn"}
 
 
 class Lattice(C.Structure):

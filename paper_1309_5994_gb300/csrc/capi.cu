@@ -34,25 +34,6 @@ double bits_to_double(unsigned long long b) {
 }
 
 // -------------------------------------------------------------------------
-// per-kernel-kind timing with events on the library stream
-// -------------------------------------------------------------------------
-struct KernelTimer {
-  dyson_ctx* c;
-  int kind;
-  cudaEvent_t a = nullptr, b = nullptr;
-  KernelTimer(dyson_ctx* cc, int k) : c(cc), kind(k) {
-    if (!c->profiling) return;
-    cudaEventCreate(&a);
-    cudaEventCreate(&b);
-    cudaEventRecord(a, c->stream);
-  }
-  ~KernelTimer() {
-    if (!a) return;
-    cudaEventRecord(b, c->stream);
-    c->pending.push_back({kind, a, b});
-  }
-};
-
 void flush_timers(dyson_ctx* c) {
   for (auto& p : c->pending) {
     float ms = 0.f;

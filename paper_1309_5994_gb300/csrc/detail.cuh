@@ -52,6 +52,25 @@ constexpr double kSeriesPeakMax = 1e5;
 // is near 1e-6; the FP64 refinement supplies the rest)
 constexpr double kGmresTarget = 4e-6;
 
+// per-kernel-kind timing with events on the library stream
+// -------------------------------------------------------------------------
+struct KernelTimer {
+  dyson_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KernelTimer(dyson_ctx* cc, int k) : c(cc), kind(k) {
+    if (!c->profiling) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->stream);
+  }
+  ~KernelTimer() {
+    if (!a) return;
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({kind, a, b});
+  }
+};
+
 int fail_noctx(int code, const std::string& m);           // error without a context
 double bits_to_double(unsigned long long b);
 void flush_timers(dyson_ctx* c);                          // fold finished event timings into the profile

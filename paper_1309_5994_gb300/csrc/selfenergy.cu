@@ -655,8 +655,11 @@ extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mi
   const size_t smem = 6 * (size_t)Nc * sizeof(double2) + 256 * PATHS * sizeof(uint32_t);
   if (smem > 48 * 1024)
     DY_CUDA(c, cudaFuncSetAttribute(k_se_conn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_se_conn<<<dim3((unsigned)((Nc * Nc + CONN_THREADS - 1) / CONN_THREADS), Nr), CONN_THREADS, smem, c->stream>>>(
-      st->paths, c->d_phase, st->FT, c->Nt, c->Nm, st->conn);
+  {
+    KernelTimer t(c, DYSON_KERNEL_SELFENERGY);
+    k_se_conn<<<dim3((unsigned)((Nc * Nc + CONN_THREADS - 1) / CONN_THREADS), Nr), CONN_THREADS, smem,
+                c->stream>>>(st->paths, c->d_phase, st->FT, c->Nt, c->Nm, st->conn);
+  }
   k_se_trace<<<Nr, 256, 0, c->stream>>>(st->g0, st->FT, Nc, st->tr);
   c->launches += 3;
   DY_CUDA(c, cudaGetLastError());
@@ -695,5 +698,6 @@ extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mi
     mx = std::max(mx, part[2 * b + 1]);
   }
   if (criterion) *criterion = std::sqrt(ss) / (double)n_el + std::sqrt(mx);
+  flush_timers(c);
   return DYSON_OK;
 }
