@@ -210,17 +210,21 @@ int dyson_local_greens(dyson_ctx* ctx, const int32_t* src_sites, int64_t n_src, 
  *   Sigma~_i(a, d) = - sum_{j in NN(i)} sum_{b, c} K_i(a, b; c, d) W_c J_ij(c) Gloc_j(c, b) J_ji(b) W_b,
  * K_i the second-order cumulant of the isolated site i summed over the
  * neighbour's spin, evaluated on the fly from the site's phases (O(Nc^4) per
- * site, FP64); then Sigma_i = W^-1 G0_i^+ Sigma~_i G0_i^+ W^-1 (G0 = the atomic
- * Lambda of the last dyson_build_sigma; the contour inverse is read with the
- * pseudo-inverse because the turning point of the discretised contour makes G0
- * singular), mixed as Sigma = mix Sigma_new + (1 - mix) Sigma_old (Sigma_old = 0
- * after dyson_build_sigma), and the local block
- *   B_i = (I - G0_i W Sigma_i W)^-1 G0_i
- * replaces Lambda_i for the following solves (all precisions).
+ * site, FP64); Sigma = G0^-1 * Sigma~ * G0^-1 (Eq. (defnSigma); G0 = the atomic
+ * Lambda of the last dyson_build_sigma) is mixed as Sigma = mix Sigma_new +
+ * (1 - mix) Sigma_old (Sigma_old = 0 after dyson_build_sigma; being linear in
+ * Sigma~, the mixing is applied to Sigma~), and the local block
+ *   B_i = G0_i (G0_i - Sigma~_i)^-1 G0_i,
+ * the solution of the local Dyson equation B = G0 + G0 * Sigma * B, replaces
+ * Lambda_i for the following solves (all precisions).  The two turning points of
+ * the discretised contour make G0 - Sigma~ singular by one rank; the system is
+ * completed along those directions, which leaves B unchanged.
  *   sigma_tilde  DEVICE [Nr][Nc][Nc] complex128 or NULL: receives Sigma~_new;
- *   criterion    host or NULL: N_bd^-1 |Sigma_new - Sigma_old|_F + |Sigma_new - Sigma_old|_max
- *                (N_bd = Nr Nc^2 block-diagonal entries), the paper's convergence measure.
- * dyson_build_sigma returns to Sigma = 0.  Device memory: 8 Nr Nc^2 complex128.
+ *   criterion    host or NULL: N_bd^-1 |Sigma~_new - Sigma~_old|_F + |Sigma~_new - Sigma~_old|_max
+ *                (N_bd = Nr Nc^2 block-diagonal entries), Sec. IV.C's measure taken on Sigma~
+ *                (Sigma itself divides by a singular value of G0 that falls exponentially
+ *                with the real-time branch length).
+ * dyson_build_sigma returns to Sigma = 0.  Device memory: 7 Nr Nc^2 complex128.
  * Returns INVALID_ARG for mix outside (0, 1] or a NULL gloc, STATE before
  * dyson_build_sigma or with Lambda transposed, DIVERGED if a local system is
  * singular.  dyson_adjoint and dyson_adjoint_obs return STATE while a local block

@@ -19,21 +19,30 @@ two-particle function is an [Nc]^4 tensor):
   the Dyson solve):
       F_i(c, b)       = sum_{j in NN(i)} W_c J_ij(c) Gloc_j(c, b) J_ji(b) W_b,
       Sigma~_i(a, d)  = - sum_{b, c} K_i(a, b; c, d) F_i(c, b);
-* Eq. (defnSigma) with contour products and inverses: the contour inverse of G0
-  is W^-1 G0^+ W^-1, so W Sigma_i W = T_i = G0_i^+ Sigma~_i G0_i^+, and the local
-  Dyson equation B = G0 + G0 W Sigma W B gives the block that replaces
-  Lambda_i = G0_i in the lattice solve,
-      B_i = (I - G0_i T_i)^-1 G0_i;
+* Eq. (defnSigma) with contour products and inverses: Sigma = G0^-1 * Sigma~ * G0^-1,
+  and the local Dyson equation B = G0 + G0 * Sigma * B gives the block that
+  replaces Lambda_i = G0_i in the lattice solve; with matrices,
+      B_i = G0_i (G0_i - Sigma~_i)^-1 G0_i,
+  which needs no inverse of G0 (see the readings for the turning points);
 * the self-consistency loop of Sec. IV.C: Sigma = lambda Sigma_new + (1 - lambda)
-  Sigma_old, converged when N_bd^-1 |Sigma_new - Sigma_old|_F + |Sigma_new -
-  Sigma_old|_max <= delta_sc (N_bd the number of block-diagonal entries).
+  Sigma_old (Sigma is linear in Sigma~, so the mixing acts on Sigma~), converged
+  when N_bd^-1 |dSigma~|_F + |dSigma~|_max <= delta_sc (N_bd the number of
+  block-diagonal entries).
 
 Readings (the paper does not fix them):
-* G0^+ is the Moore-Penrose pseudo-inverse.  On this discretised contour the
-  last forward point and the first backward point carry the same time and, by
-  the equal-point rule, G0 has two equal columns there: G0 is singular (rank
-  Nc - 1), while the continuum contour function is invertible.  With G0
-  invertible every formula above is the plain inverse.
+* The turning points of the discretised contour: the last forward and the first
+  backward point carry one time (G0 has equal columns there, right null vector
+  v = e_{Nt-1} - e_{Nt}), and so do the last backward and the first imaginary
+  point (equal rows, left null vector u = e_{2Nt-1} - e_{2Nt}); Sigma~ has the
+  same equal columns and rows.  G0 - Sigma~ is therefore singular too, and B is
+  formed as G0 (G0 - Sigma~ + u v^T / 2)^-1 G0, which does not depend on the
+  filled-in direction (B is the same for any such rank-one completion, and it
+  equals (I - G0 T)^-1 G0 with T = G0^+ Sigma~ G0^+, the pseudo-inverse form of
+  W Sigma W).  The continuum G0 is invertible; on long real-time branches its
+  matrix also has one singular value that falls exponentially with the branch
+  length (the zero of the atomic Green's function between its two levels), so
+  forming Sigma itself amplifies rounding, and the convergence measure of
+  Sec. IV.C is taken on Sigma~ (delta_sc = 1e-8 by default).
 * T_C order on the discretised contour is index order; at one contour point,
   creators count as later than annihilators on the forward and imaginary
   branches and as earlier on the backward branch (the equal-time reading of the
@@ -195,20 +204,30 @@ def sigma_tilde(S, K: np.ndarray, Gloc: np.ndarray, i: int) -> np.ndarray:
 
 
 def weighted_sigma(G0: np.ndarray, St: np.ndarray) -> np.ndarray:
-    """T = W Sigma W = G0^+ Sigma~ G0^+ (Eq. (defnSigma) with the contour inverse W^-1 G0^+ W^-1)."""
+    """T = W Sigma W = G0^+ Sigma~ G0^+ (the contour inverse read with the pseudo-inverse)."""
     Gp = np.linalg.pinv(G0, rcond=1e-12)
     return Gp @ St @ Gp
 
 
 def sigma_contour(S, G0: np.ndarray, St: np.ndarray) -> np.ndarray:
-    """Sigma = W^-1 G0^+ Sigma~ G0^+ W^-1, the contour function whose changes decide convergence."""
+    """Sigma = W^-1 G0^+ Sigma~ G0^+ W^-1 (only where G0 is well conditioned)."""
     Wi = 1.0 / S.contour.W
     return Wi[:, None] * weighted_sigma(G0, St) * Wi[None, :]
 
 
-def local_block(G0: np.ndarray, T: np.ndarray) -> np.ndarray:
-    """B = (I - G0 T)^-1 G0, the solution of the local Dyson equation B = G0 + G0 W Sigma W B."""
-    return np.linalg.solve(np.eye(G0.shape[0]) - G0 @ T, G0)
+def turning_vectors(Nt: int, Nc: int):
+    """u = (e_{2Nt-1} - e_{2Nt}) / sqrt 2, v = (e_{Nt-1} - e_{Nt}) / sqrt 2."""
+    u = np.zeros(Nc)
+    v = np.zeros(Nc)
+    u[2 * Nt - 1], u[2 * Nt] = 1.0, -1.0
+    v[Nt - 1], v[Nt] = 1.0, -1.0
+    return u / np.sqrt(2.0), v / np.sqrt(2.0)
+
+
+def local_block(G0: np.ndarray, St: np.ndarray, Nt: int) -> np.ndarray:
+    """B = G0 (G0 - Sigma~ + u v^T)^-1 G0, the solution of the local Dyson equation B = G0 + G0 * Sigma * B."""
+    u, v = turning_vectors(Nt, G0.shape[0])
+    return G0 @ np.linalg.solve(G0 - St + np.outer(u, v), G0)
 
 
 def local_greens(S, blocks: np.ndarray) -> np.ndarray:
@@ -218,31 +237,24 @@ def local_greens(S, blocks: np.ndarray) -> np.ndarray:
     return np.stack([G[j, :, j * S.Nc:(j + 1) * S.Nc] for j in range(S.Nr)])
 
 
-def self_consistent(p, mix: float = 0.7, delta_sc: float = None, max_iter: int = 40):
+def self_consistent(p, mix: float = 0.7, delta_sc: float = 1e-8, max_iter: int = 40):
     """The loop of Sec. IV.C.  Returns (blocks B_i, mixed Sigma~ per site, the last Gloc,
-    iterations, history of the criterion)."""
+    iterations, history of the measure)."""
     S = dyson.setup(p)
-    if delta_sc is None:
-        delta_sc = 1e-8 * float(np.abs(S.U).max())
     G0 = S.Lam
     Ks = [cumulant_sum(S.contour, S.eps[i], S.U[i], G0[i]) for i in range(S.Nr)]
     St = np.zeros_like(G0)
-    Sig = np.zeros_like(G0)
     blocks = G0.copy()
     hist = []
     n_bd = S.Nr * S.Nc * S.Nc
     for it in range(1, max_iter + 1):
         Gloc = local_greens(S, blocks)
         St_new = np.stack([sigma_tilde(S, Ks[i], Gloc, i) for i in range(S.Nr)])
-        Sig_new = np.stack([sigma_contour(S, G0[i], St_new[i]) for i in range(S.Nr)])
-        d = Sig_new - Sig
+        d = St_new - St
         crit = np.sqrt((np.abs(d) ** 2).sum()) / n_bd + np.abs(d).max()
         hist.append(float(crit))
-        Sig = mix * Sig_new + (1.0 - mix) * Sig                # Eq. (Sigmamix); Sigma_old = 0 at the start
-        W = S.contour.W
-        T = W[None, :, None] * Sig * W[None, None, :]
-        St = mix * St_new + (1.0 - mix) * St
-        blocks = np.stack([local_block(G0[i], T[i]) for i in range(S.Nr)])
+        St = mix * St_new + (1.0 - mix) * St                  # Eq. (Sigmamix); Sigma_old = 0 at the start
+        blocks = np.stack([local_block(G0[i], St[i], p.Nt) for i in range(S.Nr)])
         if crit <= delta_sc:
             break
     return blocks, St, Gloc, it, hist

@@ -22,16 +22,19 @@
 // (the imaginary-branch factors span exp(+-beta E); a product keeps its relative
 // precision, and every summand is a physical, bounded term).
 //
-// Then Sigma enters the lattice solve through the local block
-//   T_i = G0_i^+ Sigma~_i G0_i^+   (= W Sigma_i W; the contour inverse of G0 is W^-1 G0^+ W^-1),
-//   B_i = (I - G0_i T_i)^-1 G0_i   (the local Dyson equation B = G0 + G0 W Sigma W B),
-// which replaces Lambda_i.  G0 is singular on this contour (the last forward and
-// the first backward point carry one time and give G0 two equal columns, the
-// right null vector v = (e_{Nt-1} - e_{Nt}) / sqrt 2), so
-//   G0^+ = (G0^H G0 + v v^H)^-1 G0^H.
-// Mixing (Eq. (Sigmamix)) acts on T, a fixed linear image of Sigma; the criterion
-// N_bd^-1 |Sigma_new - Sigma_old|_F + |Sigma_new - Sigma_old|_max is evaluated on
-// Sigma = W^-1 T W^-1.
+// Then Sigma = G0^-1 * Sigma~ * G0^-1 enters the lattice solve through the local
+// Dyson equation B = G0 + G0 * Sigma * B, whose matrix solution
+//   B_i = G0_i (G0_i - Sigma~_i)^-1 G0_i
+// replaces Lambda_i and needs no inverse of G0.  On the discretised contour the
+// turning points (last forward / first backward point, last backward / first
+// imaginary point) carry one time each, so G0 and Sigma~ share equal columns
+// (right null vector v = e_{Nt-1} - e_{Nt}) and equal rows (left null vector
+// u = e_{2Nt-1} - e_{2Nt}); the singular system is completed to
+// G0 - Sigma~ + u v^T / 2, which leaves B unchanged.  Mixing (Eq. (Sigmamix)) acts
+// on Sigma~ (Sigma is linear in it), and so does the convergence measure
+// N_bd^-1 |dSigma~|_F + |dSigma~|_max: forming Sigma itself would divide by the
+// exponentially small singular value the atomic G0 develops on long real-time
+// branches.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -328,15 +331,17 @@ __global__ void k_se_combine(const double2* __restrict__ conn, const double2* __
   }
 }
 
-// M = G0^H G0 + v v^H is formed by k_zgemm; this adds v v^H at (Nt - 1, Nt)
-__global__ void k_se_add_null(double2* __restrict__ M, int Nc, int Nt) {
-  const int i = blockIdx.x;
-  if (threadIdx.x != 0) return;
-  double2* m = M + (size_t)i * Nc * Nc;
-  m[(size_t)(Nt - 1) * Nc + Nt - 1].x += 0.5;
-  m[(size_t)Nt * Nc + Nt].x += 0.5;
-  m[(size_t)(Nt - 1) * Nc + Nt].x -= 0.5;
-  m[(size_t)Nt * Nc + Nt - 1].x -= 0.5;
+// M = G0 - Sigma~ + u v^T / 2 (u = e_{2Nt-1} - e_{2Nt}, v = e_{Nt-1} - e_{Nt}): the turning-point completion
+__global__ void k_se_complete(const double2* __restrict__ g0, const double2* __restrict__ St, int Nc, int Nt,
+                              size_t total, double2* __restrict__ M) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)((e / Nc) % Nc), c = (int)(e % Nc);
+    double x = g0[e].x - St[e].x;
+    const double su = r == 2 * Nt - 1 ? 1.0 : (r == 2 * Nt ? -1.0 : 0.0);
+    const double sv = c == Nt - 1 ? 1.0 : (c == Nt ? -1.0 : 0.0);
+    x += 0.5 * su * sv;
+    M[e] = make_double2(x, g0[e].y - St[e].y);
+  }
 }
 
 // out_i = A_i^T, conjugated when conj != 0
@@ -355,14 +360,6 @@ __global__ void k_transpose(const double2* __restrict__ A, int n, int conj, doub
       const double2 v = tile[threadIdx.x][r];
       out[((size_t)i * n + row) * n + col] = make_double2(v.x, conj ? -v.y : v.y);
     }
-  }
-}
-
-// M = I - X
-__global__ void k_identity_minus(double2* __restrict__ X, int n, size_t total) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const size_t r = (e / n) % n, c = e % n;
-    X[e] = make_double2((r == c ? 1.0 : 0.0) - X[e].x, -X[e].y);
   }
 }
 
@@ -463,20 +460,17 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gauss_jordan(double2* __restrict
   if (threadIdx.x == 0 && bad) err[i] = 1;
 }
 
-// Sigma difference and mixing: dS = W^-1 (Tn - T) W^-1 folded into per-block (sum |dS|^2, max |dS|),
-// then T = lambda Tn + (1 - lambda) T
+// Sigma~ difference and mixing: (sum |dS|^2, max |dS|) per block, dS = Sn - Sm; then Sm = lambda Sn + (1 - lambda) Sm
 constexpr int MIX_BLOCKS = 1024;
-__global__ void k_se_mix(const double2* __restrict__ Tn, double2* __restrict__ T, const double2* __restrict__ winv,
-                         int Nc, size_t total, double lambda, double* __restrict__ part) {
+__global__ void k_se_mix(const double2* __restrict__ Sn, double2* __restrict__ Sm, size_t total, double lambda,
+                         double* __restrict__ part) {
   double ss = 0.0, mx = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int a = (int)((e / Nc) % Nc), d = (int)(e % Nc);
-    const double2 dt = make_double2(Tn[e].x - T[e].x, Tn[e].y - T[e].y);
-    const double2 ds = cmul(cmul(winv[a], dt), winv[d]);
-    const double m2 = ds.x * ds.x + ds.y * ds.y;
+    const double dx = Sn[e].x - Sm[e].x, dy = Sn[e].y - Sm[e].y;
+    const double m2 = dx * dx + dy * dy;
     ss += m2;
     mx = fmax(mx, m2);
-    T[e] = make_double2(lambda * Tn[e].x + (1.0 - lambda) * T[e].x, lambda * Tn[e].y + (1.0 - lambda) * T[e].y);
+    Sm[e] = make_double2(lambda * Sn[e].x + (1.0 - lambda) * Sm[e].x, lambda * Sn[e].y + (1.0 - lambda) * Sm[e].y);
   }
   __shared__ double s1[256], s2[256];
   s1[threadIdx.x] = ss;
@@ -518,18 +512,17 @@ __global__ void k_export_diagonal(const double2* __restrict__ G, const int* __re
 // ---------------------------------------------------------------------------
 struct SeState {
   int Nr = 0, Nc = 0;
-  double2 *g0 = nullptr, *g0p = nullptr, *T = nullptr, *FT = nullptr, *conn = nullptr, *w1 = nullptr,
-          *w2 = nullptr, *St = nullptr, *tr = nullptr, *winv = nullptr;
+  double2 *g0 = nullptr, *Sm = nullptr, *FT = nullptr, *conn = nullptr, *w1 = nullptr, *w2 = nullptr,
+          *St = nullptr, *tr = nullptr;
   uint32_t* paths = nullptr;
   double* part = nullptr;
   int* err = nullptr;
-  bool ready = false;                // g0 and g0p hold the atomic Lambda of the current build
+  bool ready = false;                // g0 holds the atomic Lambda of the current build, Sm the mixed Sigma~
   int steps = 0;
 };
 
 void free_state(SeState* st) {
-  void* ptrs[] = {st->g0, st->g0p, st->T, st->FT, st->conn, st->w1, st->w2, st->St, st->tr, st->winv,
-                  st->paths, st->part, st->err};
+  void* ptrs[] = {st->g0, st->Sm, st->FT, st->conn, st->w1, st->w2, st->St, st->tr, st->paths, st->part, st->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -572,7 +565,7 @@ int ensure_state(dyson_ctx* c) {
   st->Nr = c->Nr;
   st->Nc = c->Nc;
   const size_t blk = (size_t)c->Nr * c->Nc * c->Nc * sizeof(double2);
-  double2** bufs[] = {&st->g0, &st->g0p, &st->T, &st->FT, &st->conn, &st->w1, &st->w2, &st->St};
+  double2** bufs[] = {&st->g0, &st->Sm, &st->FT, &st->conn, &st->w1, &st->w2, &st->St};
   for (double2** b : bufs) {
     if (cudaMalloc(b, blk) != cudaSuccess) {
       cudaGetLastError();
@@ -580,7 +573,6 @@ int ensure_state(dyson_ctx* c) {
     }
   }
   if (cudaMalloc(&st->tr, (size_t)c->Nr * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(&st->winv, (size_t)c->Nc * sizeof(double2)) != cudaSuccess ||
       cudaMalloc(&st->paths, 256 * PATHS * sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&st->part, 2 * MIX_BLOCKS * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&st->err, (size_t)c->Nr * sizeof(int)) != cudaSuccess) {
@@ -589,29 +581,16 @@ int ensure_state(dyson_ctx* c) {
   }
   const std::vector<uint32_t> tab = path_table();
   DY_CUDA(c, cudaMemcpy(st->paths, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-  std::vector<double2> winv(c->Nc);
-  for (int z = 0; z < c->Nc; ++z) {
-    if (z < 2 * c->Nt) winv[z] = make_double2(z < c->Nt ? 1.0 / c->dt : -1.0 / c->dt, 0.0);
-    else winv[z] = make_double2(0.0, c->Nm / c->beta);   // 1 / (-i beta / Nm)
-  }
-  DY_CUDA(c, cudaMemcpy(st->winv, winv.data(), winv.size() * sizeof(double2), cudaMemcpyHostToDevice));
   return DYSON_OK;
 }
 
-// G0 = the atomic Lambda of the current build; G0^+ = (G0^H G0 + v v^H)^-1 G0^H; T = 0
+// G0 = the atomic Lambda of the current build; the mixed Sigma~ starts at 0
 int prepare(dyson_ctx* c) {
   SeState* st = state(c);
   if (st->ready) return DYSON_OK;
   const size_t blk = (size_t)c->Nr * c->Nc * c->Nc * sizeof(double2);
-  int rc;
   DY_CUDA(c, cudaMemcpyAsync(st->g0, c->d_lam, blk, cudaMemcpyDeviceToDevice, c->stream));
-  if ((rc = gemm(c, st->g0, st->g0, st->w1, 1))) return rc;            // G0^H G0
-  k_se_add_null<<<c->Nr, 32, 0, c->stream>>>(st->w1, c->Nc, c->Nt);
-  k_transpose<<<tiles32(c->Nc, c->Nr), dim3(32, 8), 0, c->stream>>>(st->g0, c->Nc, 1, st->g0p);
-  c->launches += 2;
-  DY_CUDA(c, cudaGetLastError());
-  if ((rc = solve(c, st, st->w1, st->g0p, "pseudo-inverse of the atomic block"))) return rc;
-  DY_CUDA(c, cudaMemsetAsync(st->T, 0, blk, c->stream));
+  DY_CUDA(c, cudaMemsetAsync(st->Sm, 0, blk, c->stream));
   st->ready = true;
   st->steps = 0;
   return DYSON_OK;
@@ -673,19 +652,18 @@ extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mi
   DY_CUDA(c, cudaGetLastError());
   if (sigma_tilde)
     DY_CUDA(c, cudaMemcpyAsync(sigma_tilde, st->St, n_el * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  // T_new = G0^+ Sigma~ G0^+ (into conn); criterion on Sigma = W^-1 T W^-1; T = mix T_new + (1 - mix) T
-  if ((rc = gemm(c, st->g0p, st->St, st->w1, 0)) || (rc = gemm(c, st->w1, st->g0p, st->conn, 0))) return rc;
-  k_se_mix<<<MIX_BLOCKS, 256, 0, c->stream>>>(st->conn, st->T, st->winv, Nc, n_el, mix, st->part);
+  // measure and mixing on Sigma~
+  k_se_mix<<<MIX_BLOCKS, 256, 0, c->stream>>>(st->St, st->Sm, n_el, mix, st->part);
   c->launches += 1;
   DY_CUDA(c, cudaGetLastError());
   std::vector<double> part(2 * MIX_BLOCKS);
   DY_CUDA(c, cudaMemcpyAsync(part.data(), st->part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  // B = (I - G0 T)^-1 G0 replaces Lambda
-  if ((rc = gemm(c, st->g0, st->T, st->w1, 0))) return rc;
-  k_identity_minus<<<eblocks, 256, 0, c->stream>>>(st->w1, Nc, n_el);
+  // B = G0 (G0 - Sigma~ + u v^T / 2)^-1 G0 replaces Lambda
+  k_se_complete<<<eblocks, 256, 0, c->stream>>>(st->g0, st->Sm, Nc, c->Nt, n_el, st->w1);
   c->launches += 1;
-  DY_CUDA(c, cudaMemcpyAsync(st->w2, st->g0, n_el * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  if ((rc = solve(c, st, st->w1, st->w2, "local Dyson equation"))) return rc;
+  DY_CUDA(c, cudaMemcpyAsync(st->conn, st->g0, n_el * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+  if ((rc = solve(c, st, st->w1, st->conn, "local Dyson equation"))) return rc;
+  if ((rc = gemm(c, st->g0, st->conn, st->w2, 0))) return rc;
   DY_CUDA(c, cudaMemcpyAsync(c->d_lam, st->w2, n_el * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
   c->lam32_built = c->lam_split_built = false;

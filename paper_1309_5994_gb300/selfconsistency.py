@@ -4,12 +4,10 @@ Each iteration solves the block columns of every site with the current local
 blocks (dyson_local_greens, only the diagonal blocks G_jj are kept), takes a
 self-energy step from them (dyson_selfenergy_step: Eqs. (defnSigmatilde) and
 (defnSigma), mixing of Eq. (Sigmamix), new local blocks installed) and stops when
-the paper's measure N_bd^-1 |dSigma|_F + |dSigma|_max falls to delta_sc
-(default 1e-8 times the largest U, the paper's suggestion).
+the paper's measure, taken on Sigma~, N_bd^-1 |dSigma~|_F + |dSigma~|_max, falls
+to delta_sc (default 1e-8).
 """
 from __future__ import annotations
-
-import numpy as np
 
 from . import binding
 
@@ -20,7 +18,7 @@ def self_consistent(solver, mix=0.7, delta_sc=None, max_iter=40, precision=bindi
     iteration count, the history of the measure, whether it converged, the last
     local Green's functions (device tensor [Nr, Nc, Nc]) and the solve reports."""
     if delta_sc is None:
-        delta_sc = 1e-8 * float(np.abs(solver.p.U).max())
+        delta_sc = 1e-8
     gloc = None
     hist, reports = [], []
     converged = False

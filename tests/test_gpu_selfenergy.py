@@ -49,7 +49,7 @@ def test_sigma_tilde_and_local_block_match_the_oracle(torch_cuda, lib, kw):
         K = se.cumulant_sum(S.contour, S.eps[i], S.U[i], S.Lam[i])
         ref = se.sigma_tilde(S, K, gloc, i)
         assert np.abs(got[i] - ref).max() <= 1e-12 * np.abs(ref).max(), i
-        B = se.local_block(S.Lam[i], se.weighted_sigma(S.Lam[i], ref))
+        B = se.local_block(S.Lam[i], ref, p.Nt)
         assert np.abs(lam[i] - B).max() <= 1e-10 * np.abs(B).max(), i
 
 
@@ -73,9 +73,9 @@ def test_sigma_tilde_vanishes_without_interaction(torch_cuda, lib):
 def test_self_consistent_loop_matches_the_oracle(torch_cuda, lib):
     from paper_1309_5994_gb300.selfconsistency import self_consistent
     p = wl.small(**SMALL)
-    blocks, St, Gloc, its, hist = se.self_consistent(p, mix=0.7, delta_sc=1e-10, max_iter=60)
+    blocks, St, Gloc, its, hist = se.self_consistent(p, mix=0.7, delta_sc=1e-11, max_iter=60)
     s = _solver(p)
-    r = self_consistent(s, mix=0.7, delta_sc=1e-10, max_iter=60, precision=0, tol=1e-14)
+    r = self_consistent(s, mix=0.7, delta_sc=1e-11, max_iter=60, precision=0, tol=1e-14)
     assert r["converged"] and abs(r["iterations"] - its) <= 1
     n = min(len(hist), len(r["history"]))
     h0, h1 = np.array(hist[:n - 2]), np.array(r["history"][:n - 2])
@@ -94,7 +94,7 @@ def test_mixed_precision_loop_agrees_with_fp64(torch_cuda, lib):
     for prec, tol in ((0, 1e-13), (1, 1e-11)):
         s = _solver(p)
         s.profile(True)
-        out[prec] = self_consistent(s, mix=0.7, delta_sc=1e-7, max_iter=40, precision=prec, tol=tol)
+        out[prec] = self_consistent(s, mix=0.7, delta_sc=1e-8, max_iter=40, precision=prec, tol=tol)
         if prec == 1:
             assert s.profile_query(2)[0] > 0 and s.profile_query(4)[0] > 0
         out[prec]["lam"] = s.sigma()

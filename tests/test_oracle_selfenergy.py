@@ -67,34 +67,39 @@ def test_equal_point_values_are_the_atomic_occupations(grid):
         assert abs(G2o[z, z, z, z] - want) < 1e-14
 
 
-def test_turning_point_makes_the_atomic_matrix_singular():
-    """The last forward and the first backward point carry the same time, and by the equal-point
-    rule G0 has equal columns there: rank Nc - 1, every other singular value O(1)."""
+def test_turning_points_make_the_atomic_matrix_singular():
+    """The last forward and the first backward point carry one time, and so do the last backward
+    and the first imaginary point: G0 has equal columns at the first pair and equal rows at the
+    second, rank Nc - 1; Sigma~ has the same structure."""
     p = wl.small(L=2, Ly=1, Nt=5, Nm=4, dt=0.1, aU=0.1, aJ=0.2, omega=5.0)
     S = dyson.setup(p)
     G0 = S.Lam[0]
     Nt = p.Nt
-    assert np.array_equal(G0[:, Nt - 1], G0[:, Nt])
+    assert np.array_equal(G0[:, Nt - 1], G0[:, Nt]) and np.array_equal(G0[2 * Nt - 1], G0[2 * Nt])
     sv = np.linalg.svd(G0, compute_uv=False)
     assert sv[-1] < 1e-14 * sv[0] and sv[-2] > 0.1
+    St = se.sigma_tilde(S, se.cumulant_sum(S.contour, S.eps[0], S.U[0], G0), S.Lam, 0)
+    assert np.abs(St[:, Nt - 1] - St[:, Nt]).max() < 1e-15 and np.abs(St[2 * Nt - 1] - St[2 * Nt]).max() < 1e-15
 
 
 def test_local_block_solves_the_local_dyson_equation():
-    """B = (I - G0 T)^-1 G0 satisfies B = G0 + G0 W Sigma W B with W Sigma W = T = G0^+ Sigma~ G0^+,
-    and for an invertible G0 it is G0 (G0 - Sigma~)^-1 G0."""
+    """B = G0 (G0 - Sigma~ + u v^T)^-1 G0 equals (I - G0 T)^-1 G0 with T = G0^+ Sigma~ G0^+, i.e. it
+    satisfies B = G0 + G0 W Sigma W B with Sigma = W^-1 G0^+ Sigma~ G0^+ W^-1 (where G0 is well
+    conditioned), and for an invertible G0 it is G0 (G0 - Sigma~)^-1 G0."""
     p = wl.small(L=2, Ly=1, Nt=5, Nm=4, dt=0.1, aU=0.1, aJ=0.2, omega=5.0)
     S = dyson.setup(p)
-    rng = np.random.default_rng(4)
     G0 = S.Lam[0]
-    St = 0.05 * (rng.normal(size=G0.shape) + 1j * rng.normal(size=G0.shape))
-    T = se.weighted_sigma(G0, St)
-    B = se.local_block(G0, T)
+    St = se.sigma_tilde(S, se.cumulant_sum(S.contour, S.eps[0], S.U[0], G0), S.Lam, 0)
+    B = se.local_block(G0, St, p.Nt)
     Sig = se.sigma_contour(S, G0, St)
     W = S.contour.W
     assert np.abs(B - G0 - G0 @ (W[:, None] * Sig * W[None, :]) @ B).max() < 1e-12 * np.abs(B).max()
+    rng = np.random.default_rng(4)
     A = G0 + 0.3 * np.eye(G0.shape[0])                     # invertible: the plain-inverse form
-    Ba = se.local_block(A, se.weighted_sigma(A, St))
-    assert np.abs(Ba - A @ np.linalg.solve(A - St, A)).max() < 1e-11 * np.abs(Ba).max()
+    R = 0.05 * (rng.normal(size=G0.shape) + 1j * rng.normal(size=G0.shape))
+    T = np.linalg.solve(A, np.linalg.solve(A.T, R.T).T)   # A^-1 R A^-1
+    Ba = np.linalg.solve(np.eye(A.shape[0]) - A @ T, A)
+    assert np.abs(Ba - A @ np.linalg.solve(A - R, A)).max() < 1e-11 * np.abs(Ba).max()
 
 
 def test_sigma_tilde_vanishes_at_zero_hopping_and_scales_as_J_squared():
@@ -115,8 +120,8 @@ def test_sigma_tilde_vanishes_at_zero_hopping_and_scales_as_J_squared():
 def test_self_consistency_converges_to_a_fixed_point():
     """The loop of Sec. IV.C reaches the criterion, and its result reproduces itself."""
     p = wl.small(L=2, Ly=2, Nt=4, Nm=3, dt=0.1, U0=8.0, J0=0.5, trap_c=0.2, aU=0.1, aJ=0.2, omega=5.0)
-    blocks, St, Gloc, its, hist = se.self_consistent(p, mix=0.7, delta_sc=1e-10, max_iter=60)
-    assert hist[-1] <= 1e-10 and its < 60
+    blocks, St, Gloc, its, hist = se.self_consistent(p, mix=0.7, delta_sc=1e-11, max_iter=60)
+    assert hist[-1] <= 1e-11 and its < 60
     S = dyson.setup(p)
     G2 = se.local_greens(S, blocks)
     St2 = np.stack([se.sigma_tilde(S, se.cumulant_sum(S.contour, S.eps[i], S.U[i], S.Lam[i]), G2, i)
