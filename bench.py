@@ -488,8 +488,9 @@ def run_gb300(args, rank, world, local):
             s2.set_sweep_variant(tuning["sweep_variant"])
             s2.set_chunk(tuning["chunk_block_columns"])
             s2.build_sigma()
-            s2.solve(dist.step_sources(p.Nr, args.batch, rank, world, k), precision=PREC, tol=args.tol,
-                     max_sweeps=400)
+            # the same source batches as the timed device steps
+            s2.solve(dist.step_sources(p.Nr, args.batch, rank, world, args.warmup + k), precision=PREC,
+                     tol=args.tol, max_sweeps=400)
             s2.observables()
             s2.close()
         torch.cuda.synchronize(dev)

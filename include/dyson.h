@@ -312,8 +312,10 @@ int dyson_set_symmetry(dyson_ctx* ctx, int mode);
  * contour allows (DYSON_SWEEP_SINGLE_CTA; DYSON_SWEEP_CTA_PAIR where Nc is a
  * multiple of 128) times every chunk of 1, 2, 4, ... block columns up to
  * max_block_columns and to what fits in 85 % of free device memory.  Then it
- * sets the context to the fastest (dyson_set_sweep_variant and dyson_set_chunk)
- * and, when out is not NULL, reports the choice and every candidate's measured
+ * sets the context to the fastest (dyson_set_sweep_variant and dyson_set_chunk;
+ * candidates are tried largest chunk first, single CTA before pair, and a later
+ * one wins only when it is more than 2 % faster, so that timing noise does not
+ * flip the choice) and, when out is not NULL, reports the choice and every candidate's measured
  * sweep throughput in vector columns per second.  Needs a built, upright Lambda
  * and Nc % 64 == 0; the work buffers keep the largest candidate's size. */
 enum { DYSON_TUNE_MAX_CANDIDATES = 32 };

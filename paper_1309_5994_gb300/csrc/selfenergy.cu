@@ -17,10 +17,12 @@
 // creator's point c passes a, b or d, so c runs through at most four intervals,
 // each with one operator order.  A host-built table gives, for each order, spin
 // case and initial state, the fermionic sign and the four channels; the kernel
-// adds per interval the coefficient of exp(i Phi_p(c)) F(c, b) for p = 1, 2 and
-// then sweeps c once.  O(Nc^4) per site, as in the paper, all products in FP64
-// (the imaginary-branch factors span exp(+-beta E); a product keeps its relative
-// precision, and every summand is a physical, bounded term).
+// adds per interval the coefficient of exp(i Phi_p(c)) F(c, b) for p = 1, 2.  The
+// interval sums over the real branches come from prefix sums over c (unit-modulus
+// factors there, so no cancellation), the imaginary branch is summed directly:
+// O(Nc^3 (1 + Nm)) per site instead of the paper's O(Nc^4), all in FP64 (the
+// imaginary-branch factors span exp(+-beta E); there each summand is a product,
+// which keeps its relative precision, and a physical, bounded term).
 //
 // Then Sigma = G0^-1 * Sigma~ * G0^-1 enters the lattice solve through the local
 // Dyson equation B = G0 + G0 * Sigma * B, whose matrix solution
@@ -160,20 +162,46 @@ __global__ void k_se_hyb(const double2* __restrict__ gloc, const double2* __rest
   }
 }
 
+// Prefix sums over the real branches of the creator terms:
+// Q_i[p][b][c] = sum_{c' < c} exp(+i Phi_p(c')) F_i(c', b),  c = 0..2Nt (2Nt + 1 entries).
+// On the real branches |exp(+i Phi)| = 1, so differences of these sums lose nothing to
+// cancellation; the imaginary branch, whose factors span exp(+-beta E), is summed directly.
+__global__ void k_se_prefix(const double2* __restrict__ phase, const double2* __restrict__ FT, int Nt, int Nm,
+                            double2* __restrict__ Q) {
+  const int Nc = 2 * Nt + Nm, R = 2 * Nt;
+  const int i = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * Nc) return;
+  const int p = t / Nc, b = t % Nc;
+  const double2* ph = phase + (size_t)i * (2 * Nc + 2) + (size_t)p * Nc;
+  const double2* f = FT + ((size_t)i * Nc + b) * Nc;
+  double2* q = Q + (((size_t)i * 2 + p) * Nc + b) * (R + 1);
+  double2 acc = make_double2(0.0, 0.0);
+  q[0] = acc;
+  for (int c = 0; c < R; ++c) {
+    acc = cfma(cexp_phase(ph[c], -1.0), f[c], acc);
+    q[c + 1] = acc;
+  }
+}
+
 // connected part: conn_i(a, d) = sum_{b,c} [G2_{up up} + G2_{up dn}](a, b; c, d) F_i(c, b)
-// grid (ceil(Nc^2 / 256), Nr), 256 threads, one (a, d) per thread
+// grid (ceil(Nc^2 / 256), Nr), 256 threads, one (a, d) per thread.  Per b the creator point c
+// runs through four intervals of fixed operator order: their real-branch parts come from the
+// prefix sums Q, their imaginary-branch parts are summed directly.
 constexpr int CONN_THREADS = 256;
 __global__ void __launch_bounds__(CONN_THREADS) k_se_conn(const uint32_t* __restrict__ paths,
                                                            const double2* __restrict__ phase,
-                                                           const double2* __restrict__ FT, int Nt, int Nm,
+                                                           const double2* __restrict__ FT,
+                                                           const double2* __restrict__ Q, int Nt, int Nm,
                                                            double2* __restrict__ conn) {
   extern __shared__ double2 sm[];
-  const int Nc = 2 * Nt + Nm;
+  const int Nc = 2 * Nt + Nm, R = 2 * Nt;
   const int i = blockIdx.y;
   double2* em = sm;                  // [2][Nc] exp(-i Phi_p(z)): annihilator factors
   double2* ep = em + 2 * Nc;         // [2][Nc] exp(+i Phi_p(z)): creator factors
-  double2* P = ep + 2 * Nc;          // [2][Nc] exp(+i Phi_p(c)) F(c, b) of the current b
-  uint32_t* tab = reinterpret_cast<uint32_t*>(P + 2 * Nc);   // [256][PATHS]
+  double2* Qs = ep + 2 * Nc;         // [2][R + 1] prefix sums of the current b
+  double2* Pi = Qs + 2 * (R + 1);    // [2][Nm] exp(+i Phi_p(c)) F(c, b) on the imaginary branch
+  uint32_t* tab = reinterpret_cast<uint32_t*>(Pi + 2 * Nm);   // [256][PATHS]
   __shared__ double rho[3];
   const double2* ph = phase + (size_t)i * (2 * Nc + 2);
   for (int e = threadIdx.x; e < 2 * Nc; e += blockDim.x) {
@@ -193,15 +221,24 @@ __global__ void __launch_bounds__(CONN_THREADS) k_se_conn(const uint32_t* __rest
   const int Ka = key_ann(a, Nt, 0), Kd = key_cre(d, Nt, 3);
   double2 acc = make_double2(0.0, 0.0);
   __syncthreads();
-  const double2 fa0 = em[a], fa1 = em[Nc + a];          // annihilator at a, channels 1 and 2
-  const double2 fd0 = ep[d], fd1 = ep[Nc + d];          // creator at d
+  // products of the factors at a and d for the four channel pairs (pa, pd)
+  double2 fad[4];
+#pragma unroll
+  for (int pa = 0; pa < 2; ++pa)
+#pragma unroll
+    for (int pd = 0; pd < 2; ++pd) fad[pa * 2 + pd] = cmul(em[pa * Nc + a], ep[pd * Nc + d]);
   const double2* Fi = FT + (size_t)i * Nc * Nc;
+  const double2* Qi = Q + (size_t)i * 2 * Nc * (R + 1);
   for (int b = 0; b < Nc; ++b) {
-    __syncthreads();                                   // the previous b's P is no longer read
-    for (int c = threadIdx.x; c < Nc; c += blockDim.x) {
-      const double2 f = Fi[(size_t)b * Nc + c];
-      P[c] = cmul(ep[c], f);
-      P[Nc + c] = cmul(ep[Nc + c], f);
+    __syncthreads();                                   // the previous b's tables are no longer read
+    for (int x = threadIdx.x; x < 2 * (R + 1); x += blockDim.x) {
+      const int p = x / (R + 1), c = x % (R + 1);
+      Qs[x] = Qi[((size_t)p * Nc + b) * (R + 1) + c];
+    }
+    for (int x = threadIdx.x; x < Nm; x += blockDim.x) {
+      const double2 f = Fi[(size_t)b * Nc + R + x];
+      Pi[x] = cmul(ep[R + x], f);
+      Pi[Nm + x] = cmul(ep[Nc + R + x], f);
     }
     __syncthreads();
     const int Kb = key_ann(b, Nt, 1);
@@ -228,7 +265,9 @@ __global__ void __launch_bounds__(CONN_THREADS) k_se_conn(const uint32_t* __rest
         const uint32_t t = tab[code * PATHS + q];
         if (!(t & 1u)) continue;
         const double w = ((t & 2u) ? -1.0 : 1.0) * rho[(t >> 6) & 3u];
-        double2 v = cmul(cmul((t & 4u) ? fa1 : fa0, (t & 8u) ? fb1 : fb0), (t & 32u) ? fd1 : fd0);
+        const int pad = ((t & 4u) ? 2 : 0) + ((t & 32u) ? 1 : 0);
+        const double2 f1 = pad == 0 ? fad[0] : pad == 1 ? fad[1] : pad == 2 ? fad[2] : fad[3];
+        double2 v = cmul(f1, (t & 8u) ? fb1 : fb0);
         v.x *= w;
         v.y *= w;
         if (t & 16u) s2 = cadd(s2, v);
@@ -237,19 +276,24 @@ __global__ void __launch_bounds__(CONN_THREADS) k_se_conn(const uint32_t* __rest
       A[iv][0] = s1;
       A[iv][1] = s2;
     }
-    // sweep c: [0, n2) interval 0, [n2, n1) 1, [n1, n0) 2, [n0, Nc) 3
+    // real branches: interval iv covers [lo, hi) with lo/hi from (0, n2, n1, n0, Nc), clipped to R
     {
-      double2 x0 = A[0][0], x1 = A[0][1];
-      for (int c = 0; c < n2; ++c) acc = cfma(x0, P[c], cfma(x1, P[Nc + c], acc));
-      x0 = A[1][0];
-      x1 = A[1][1];
-      for (int c = n2; c < n1; ++c) acc = cfma(x0, P[c], cfma(x1, P[Nc + c], acc));
-      x0 = A[2][0];
-      x1 = A[2][1];
-      for (int c = n1; c < n0; ++c) acc = cfma(x0, P[c], cfma(x1, P[Nc + c], acc));
-      x0 = A[3][0];
-      x1 = A[3][1];
-      for (int c = n0; c < Nc; ++c) acc = cfma(x0, P[c], cfma(x1, P[Nc + c], acc));
+      const int bnd[5] = {0, min(n2, R), min(n1, R), min(n0, R), R};
+#pragma unroll
+      for (int iv = 0; iv < 4; ++iv) {
+        const double2 q1 = make_double2(Qs[bnd[iv + 1]].x - Qs[bnd[iv]].x, Qs[bnd[iv + 1]].y - Qs[bnd[iv]].y);
+        const double2 q2 = make_double2(Qs[R + 1 + bnd[iv + 1]].x - Qs[R + 1 + bnd[iv]].x,
+                                        Qs[R + 1 + bnd[iv + 1]].y - Qs[R + 1 + bnd[iv]].y);
+        acc = cfma(A[iv][0], q1, cfma(A[iv][1], q2, acc));
+      }
+    }
+    // imaginary branch: direct
+    for (int x = 0; x < Nm; ++x) {
+      const int c = R + x;
+      const bool g0 = c >= n0, g1 = c >= n1, g2 = c >= n2;
+      const double2 x0 = g0 ? A[3][0] : g1 ? A[2][0] : g2 ? A[1][0] : A[0][0];
+      const double2 x1 = g0 ? A[3][1] : g1 ? A[2][1] : g2 ? A[1][1] : A[0][1];
+      acc = cfma(x0, Pi[x], cfma(x1, Pi[Nm + x], acc));
     }
   }
   if (live) conn[((size_t)i * Nc + a) * Nc + d] = acc;
@@ -513,7 +557,7 @@ __global__ void k_export_diagonal(const double2* __restrict__ G, const int* __re
 struct SeState {
   int Nr = 0, Nc = 0;
   double2 *g0 = nullptr, *Sm = nullptr, *FT = nullptr, *conn = nullptr, *w1 = nullptr, *w2 = nullptr,
-          *St = nullptr, *tr = nullptr;
+          *St = nullptr, *tr = nullptr, *Q = nullptr;
   uint32_t* paths = nullptr;
   double* part = nullptr;
   int* err = nullptr;
@@ -522,7 +566,8 @@ struct SeState {
 };
 
 void free_state(SeState* st) {
-  void* ptrs[] = {st->g0, st->Sm, st->FT, st->conn, st->w1, st->w2, st->St, st->tr, st->paths, st->part, st->err};
+  void* ptrs[] = {st->g0, st->Sm, st->FT, st->conn, st->w1, st->w2, st->St, st->tr, st->Q, st->paths, st->part,
+                  st->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -572,7 +617,8 @@ int ensure_state(dyson_ctx* c) {
       return ctx_fail(c, DYSON_ERR_OOM, "self-energy buffers");
     }
   }
-  if (cudaMalloc(&st->tr, (size_t)c->Nr * sizeof(double2)) != cudaSuccess ||
+  if (cudaMalloc(&st->Q, (size_t)c->Nr * 2 * c->Nc * (2 * c->Nt + 1) * sizeof(double2)) != cudaSuccess ||
+      cudaMalloc(&st->tr, (size_t)c->Nr * sizeof(double2)) != cudaSuccess ||
       cudaMalloc(&st->paths, 256 * PATHS * sizeof(uint32_t)) != cudaSuccess ||
       cudaMalloc(&st->part, 2 * MIX_BLOCKS * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&st->err, (size_t)c->Nr * sizeof(int)) != cudaSuccess) {
@@ -631,16 +677,20 @@ extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mi
   const double2* G = reinterpret_cast<const double2*>(gloc);
   // F (transposed), the connected contraction, the disconnected terms
   k_se_hyb<<<tiles32(Nc, Nr), dim3(32, 8), 0, c->stream>>>(G, c->d_JW, c->d_nbr, c->d_nbond, Nc, st->FT);
-  const size_t smem = 6 * (size_t)Nc * sizeof(double2) + 256 * PATHS * sizeof(uint32_t);
+  const int R = 2 * c->Nt;
+  const size_t smem = (4 * (size_t)Nc + 2 * (R + 1) + 2 * (size_t)c->Nm) * sizeof(double2) +
+                      256 * PATHS * sizeof(uint32_t);
   if (smem > 48 * 1024)
     DY_CUDA(c, cudaFuncSetAttribute(k_se_conn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     KernelTimer t(c, DYSON_KERNEL_SELFENERGY);
+    k_se_prefix<<<dim3((unsigned)((2 * Nc + 127) / 128), Nr), 128, 0, c->stream>>>(c->d_phase, st->FT, c->Nt,
+                                                                                  c->Nm, st->Q);
     k_se_conn<<<dim3((unsigned)((Nc * Nc + CONN_THREADS - 1) / CONN_THREADS), Nr), CONN_THREADS, smem,
-                c->stream>>>(st->paths, c->d_phase, st->FT, c->Nt, c->Nm, st->conn);
+                c->stream>>>(st->paths, c->d_phase, st->FT, st->Q, c->Nt, c->Nm, st->conn);
   }
   k_se_trace<<<Nr, 256, 0, c->stream>>>(st->g0, st->FT, Nc, st->tr);
-  c->launches += 3;
+  c->launches += 4;
   DY_CUDA(c, cudaGetLastError());
   // D1 = G0 F G0 (F = FT^T), Sigma~ = -conn - D1 + 2 tr(G0 F) G0
   k_transpose<<<tiles32(Nc, Nr), dim3(32, 8), 0, c->stream>>>(st->FT, Nc, 0, st->w2);
