@@ -339,7 +339,8 @@ int dyson_autotune(dyson_ctx* ctx, int32_t max_block_columns, dyson_tuning* out)
  *           and fewer when the Krylov basis does not fit in free memory);
  *   AUTO    (the default) the series, switching to GMRES for the rest of a chunk
  *           when the series diverges, its transient peak leaves FP32 no correct
- *           digit (long contours), or the refined residual grows.
+ *           digit (long contours), it runs through max_sweeps in one refinement
+ *           (spectral radius near 1), or the refined residual grows.
  * GMRES keeps restart + 4 FP32 chunk states (8 Nr Nc bytes per vector column
  * each).  The FP64 path (DYSON_PREC_F64) always runs the series.
  * Returns INVALID_ARG for an unknown solver or a restart outside 0..60. */

@@ -168,7 +168,9 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
 // while every column of r32 is zero off its source site
 int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float* da, float* db, int max_sweeps,
                 const std::vector<double>& rref, float** dres, dyson_report* rep, double* peak_out,
-                double abort_peak = std::numeric_limits<double>::infinity(), const int* act = nullptr) {
+                double abort_peak = std::numeric_limits<double>::infinity(), const int* act = nullptr,
+                bool* exhausted = nullptr) {
+  if (exhausted) *exhausted = false;
   const int ng = ncol / gs;
   const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
   DY_CUDA(c, cudaMemcpyAsync(da, r32, n32 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
@@ -217,6 +219,7 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
     }
     if (upd <= kInnerTarget) break;
     if (since_best >= kStallSweeps && best < kStallDrop * peak) break;
+    if (sweep == max_sweeps && exhausted) *exhausted = true;
   }
   *dres = da;
   if (peak_out) *peak_out = peak;
@@ -317,7 +320,7 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
   // inner solver: the series of App. C, or its GMRES.  AUTO starts with the series
   // and switches to GMRES for the rest of the chunk when the series cannot serve:
   // it diverges, its transient peak times the FP32 rounding leaves no correct
-  // digit, or the refined residual grows.
+  // digit, it uses its whole sweep budget, or the refined residual grows.
   bool gmres = c->inner_solver == DYSON_INNER_GMRES;
   const bool may_switch = c->inner_solver == DYSON_INNER_AUTO;
   const MatvecFn mv = [&](const float* zero, const float* in, float* out) {
@@ -335,13 +338,17 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
       const int* act = ref == 0 && c->support_trunc && c->use_tc && precision == DYSON_PREC_TF32X3_F64REF
                            ? support_table(c, ncol)
                            : nullptr;
+      bool exhausted = false;
       rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep, &peak,
-                       may_switch ? kSeriesPeakMax : std::numeric_limits<double>::infinity(), act);
+                       may_switch ? kSeriesPeakMax : std::numeric_limits<double>::infinity(), act, &exhausted);
       if (rc == DYSON_ERR_DIVERGED && may_switch) {
         gmres = true;                                    // redo this refinement with GMRES
         --ref;
         continue;
       }
+      // a series that used its whole sweep budget converges too slowly (spectral radius
+      // near 1): its correction is kept, the following refinements use GMRES
+      if (rc == DYSON_OK && exhausted && may_switch) gmres = true;
     }
     if (rc == DYSON_ERR_DIVERGED) {
       status = rc;

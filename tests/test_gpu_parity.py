@@ -250,13 +250,23 @@ def test_error_codes(torch_cuda, lib):
 def test_slow_series_reports_not_converged(torch_cuda, lib):
     """One imaginary point at beta = 1 puts the Matsubara block's spectral radius
     at 0.997: the series needs thousands of sweeps and the solve says so."""
+    from paper_1309_5994_gb300 import binding
     p = wl.small(L=2, Ly=2, Nt=3, Nm=1)
     s = _solver(p)
+    s.set_inner_solver(binding.INNER_SERIES)
     for prec in (0, 1):
         r = s.solve([0, 1], precision=prec, tol=1e-12, max_sweeps=50, allow=(-3,))
         assert r.status == -3
     n, _, _ = s.observables()
     assert np.all(np.isfinite(n[:2]))
+    # AUTO: a series that runs through its sweep budget hands the chunk over to GMRES
+    s.set_inner_solver(binding.INNER_AUTO)
+    got, r = _solve(torch_cuda, s, p, [0, 1], 1, tol=1e-12, max_sweeps=50)
+    assert r.status == 0 and r.report["inner_gmres"] == 1
+    S = dyson.setup(p)
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, [0, 1]))
+    for q in range(2):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-10
 
 
 DIVERGENT = dict(L=3, Ly=3, Nt=24, Nm=16, dt=0.05, beta=2.0, trap_c=0.0, U0=4.0, J0=2.0)   # rho(K) = 1.41
