@@ -187,16 +187,20 @@ def test_c4v_wedge_solve_equals_the_full_solve(torch_cuda, lib):
 
 def test_autotune_picks_a_measured_candidate_and_solves(torch_cuda, lib):
     """Nc = 128: the tuner times both sweep variants over chunks of 1, 2, 4, 6 block
-    columns, keeps the fastest, and the solve under that choice still equals the
-    dense solve."""
+    columns, keeps the fastest (within its 2 % margin), and the solve under that
+    choice still equals the dense solve."""
     p = wl.random_tables(wl.small(**TC_CASES[1]), seed=23, rel=0.2)
     S = dyson.setup(p)
     s = _solver(p)
     t = s.autotune(6)
     cands = t["candidates"]
     assert {c["chunk"] for c in cands} == {1, 2, 4, 6} and {c["variant"] for c in cands} == {0, 1}
-    best = max(cands, key=lambda c: c["vector_columns_per_s"])
+    best = cands[0]                  # the documented rule: a later candidate wins only when > 2 % faster
+    for c in cands[1:]:
+        if c["vector_columns_per_s"] > 1.02 * best["vector_columns_per_s"]:
+            best = c
     assert (t["sweep_variant"], t["chunk_block_columns"]) == (best["variant"], best["chunk"])
+    assert 1.02 * t["vector_columns_per_s"] >= max(c["vector_columns_per_s"] for c in cands)
     assert all(c["vector_columns_per_s"] > 0 for c in cands)
     sources = list(range(p.Nr))
     got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
