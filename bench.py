@@ -56,6 +56,9 @@ def parse():
                     help="instances of the seeded uneven batch in the batched-solve leg (0 skips it)")
     ap.add_argument("--no-driven", action="store_true", help="skip the driven 32x32 (Nc = 384) leg")
     ap.add_argument("--no-selfenergy", action="store_true", help="skip the self-consistency loop leg")
+    ap.add_argument("--sweep-variant", default="auto", choices=["auto", "single_cta", "cta_pair"],
+                    help="override the autotuner's sweep variant (profiling runs: kernel timings under a "
+                         "profiler can flip the tuner's choice)")
     ap.add_argument("--lattice", type=int, default=16,
                     help="lattice side; 16 is the benchmark workload, smaller sides serve ncu captures only")
     return ap.parse_args()
@@ -394,6 +397,9 @@ def run_gb300(args, rank, world, local):
     # sweep variant and chunk picked by the library's autotuner on this workload
     solver.build_sigma()
     tuning = solver.autotune(args.batch)
+    if args.sweep_variant != "auto":
+        tuning["sweep_variant"] = ["single_cta", "cta_pair"].index(args.sweep_variant)
+        solver.set_sweep_variant(tuning["sweep_variant"])
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize(dev)
@@ -566,6 +572,7 @@ def run_gb300(args, rank, world, local):
             "vector_columns_per_s": value * Nc,
             "sweeps_per_step": sweeps, "refinements_per_step": refinements, "max_rel_residual": residual,
             "autotune": {"sweep_variant": ["single_cta", "cta_pair"][tuning["sweep_variant"]],
+                         "variant_pinned": args.sweep_variant != "auto",
                          "chunk_block_columns": tuning["chunk_block_columns"],
                          "candidates": [(["single_cta", "cta_pair"][c["variant"]], c["chunk"],
                                          round(c["vector_columns_per_s"])) for c in tuning["candidates"]]},
