@@ -387,7 +387,7 @@ int dyson_batch_solve(dyson_batch* b, const int32_t* const* src, const int32_t* 
       launch_accumulate(X.G, d, c->Nr, c->Nc, X.ncol, c->stream);
       c->launches += 1;
       DYB_CUDA(b, cudaMemsetAsync(c->d_norm, 0, (size_t)X.ng * sizeof(unsigned long long), c->stream));
-      if ((rc = oz_residual(c, X.ncol, c->Nc, X.G, X.r32))) return bfail(b, rc, c->err);
+      if ((rc = oz_residual(c, X.ncol, c->Nc, X.G, X.r32, tol))) return bfail(b, rc, c->err);
     }
     for (int k = 0; k < n; ++k) {
       Inst& X = I[k];

@@ -360,7 +360,7 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
     if (c->use_oz) {
       KernelTimer t(c, DYSON_KERNEL_RESIDUAL_SPLIT);
-      if ((rc = oz_residual(c, ncol, gs, G, r32))) return rc;
+      if ((rc = oz_residual(c, ncol, gs, G, r32, tol))) return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_RESIDUAL_F64);
       launch_sweep_f64(c->d_lam, c->d_JW, c->d_nbr, c->d_nbond, G, nullptr, r32, c->d_src_site, c->d_src_time,

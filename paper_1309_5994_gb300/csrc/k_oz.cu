@@ -13,7 +13,11 @@
 // The 28 products with s + t <= 8 (truncation ~2^-50 of |A||X|) accumulate per
 // diagonal in five TMEM accumulators, {2}, {3}, {4}, {5} exact and {6, 7, 8}
 // rounded at 2^-24 of its own size (about 2^-48 of the result).  The epilogue
-// adds them in FP64, rescales, and forms r = B + A X - G in FP64.
+// adds them in FP64, rescales, and forms r = B + A X - G in FP64.  Solves whose
+// tolerance is 1e-8 or looser use the first five slices of each operand and the
+// 15 products with s + t <= 6 (digits are peeled from the top, so five slices are
+// the same numbers; truncation ~2^-35 of |A||X|, two orders below such a
+// tolerance).
 //
 // Kernels: k_oz_aprep (once per Lambda), k_oz_xprep (gather + scale + slice of X
 // per residual), k_oz_gemm (TMA + tcgen05.mma kind::f16 + FP64 epilogue).
@@ -26,7 +30,9 @@
 
 namespace {
 
-constexpr int S = 7;
+constexpr int S = 7;                                      // slices stored
+constexpr int S_SHORT = 5;                                 // slices used for tolerances >= 1e-8
+constexpr double SHORT_TOL = 1e-8;
 constexpr int BM = 128, BN = 96, BK = 32;                 // BK bf16 = 64-byte rows (64-byte swizzle)
 constexpr int A_TILE = BM * BK * 2;                       // 8 KB per A slice tile
 constexpr int X_TILE = BN * BK * 2;                       // 6 KB per X slice tile
@@ -36,7 +42,7 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr int THREADS = 256;
 constexpr int NACC = 5;                                    // diagonals {2}, {3}, {4}, {5}, {6, 7, 8}
 constexpr uint32_t TMEM_COLS = 512;                        // 5 accumulators x 96 columns
-constexpr int NPROD = S * (S + 1) / 2;                     // products with s + t <= S + 1
+
 // kind::f16, D = F32, A = B = BF16, K-major, M = 128, N = 96
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
@@ -76,7 +82,8 @@ constexpr int FIX = 7 * S;                                 // fixed-point bits o
 // then cut into signed 7-bit digits with integer shifts: slice s holds
 // q_s 2^{-7 s}, q_s = round(V_rem / 2^{7 (S - s)}), |q_1| <= 128, |q_s| <= 64.
 // Only one FP64 multiply and one conversion per value: FP64 is scarce here.
-__device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_bfloat16* dst, size_t slice_stride) {
+__device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_bfloat16* dst, size_t slice_stride,
+                                             int nslices = S) {
   long long V = __double2ll_rn(x * fix_over_sc);
 #pragma unroll
   for (int s = 1; s <= S; ++s) {
@@ -84,7 +91,7 @@ __device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_
     const long long q = sh ? ((V + (1LL << (sh - 1))) >> sh) : V;
     V -= q << sh;
     const float part = __int2float_rn((int)q) * __int_as_float((127 - 7 * s) << 23);   // q * 2^{-7 s}, exact
-    dst[(size_t)(s - 1) * slice_stride] = __float2bfloat16_rn(part);
+    if (s <= nslices) dst[(size_t)(s - 1) * slice_stride] = __float2bfloat16_rn(part);
   }
 }
 
@@ -132,7 +139,7 @@ __global__ void k_oz_aprep(const double2* __restrict__ lam, int Nr, int Nt, int 
 
 // one warp per (site i, vector column n): X = sum_j J_ij G_j (FP64), column scale, slices
 __global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restrict__ Jtab, const int* __restrict__ nbr,
-                           const int* __restrict__ nbond, int Nr, int Nt, int Nc, int ncol,
+                           const int* __restrict__ nbond, int Nr, int Nt, int Nc, int ncol, int nslices,
                            __nv_bfloat16* __restrict__ xs, double* __restrict__ tau) {
   const size_t w = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
@@ -177,8 +184,8 @@ __global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restri
   for (int u = 0; u < PER_LANE; ++u) {
     const int z = lane + 32 * u;
     if (z < Nc) {
-      write_slices(x[u].x, fix_over_sc, dst + z, stride);
-      write_slices(x[u].y, fix_over_sc, dst + Nc + z, stride);
+      write_slices(x[u].x, fix_over_sc, dst + z, stride, nslices);
+      write_slices(x[u].y, fix_over_sc, dst + Nc + z, stride, nslices);
     }
   }
 }
@@ -186,19 +193,21 @@ __global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restri
 struct Prod {
   int s, t, acc;
 };
+template <int SE>
 __host__ __device__ constexpr Prod prod_of(int p) {
-  // products with s + t <= 7 ordered by diagonal; accumulator min(d - 2, 3)
+  // products of the first SE slices with s + t <= SE + 1, ordered by diagonal; accumulator min(d - 2, 4)
   int idx = 0;
-  for (int d = 2; d <= S + 1; ++d)
+  for (int d = 2; d <= SE + 1; ++d)
     for (int s = 1; s < d; ++s) {
       int t = d - s;
-      if (s > S || t > S) continue;
+      if (s > SE || t > SE) continue;
       if (idx == p) return Prod{s, t, d - 2 < NACC - 1 ? d - 2 : NACC - 1};
       ++idx;
     }
   return Prod{0, 0, 0};
 }
 
+template <int SE>
 __global__ void __launch_bounds__(THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap xmap,
               const double* __restrict__ sigma, const double* __restrict__ tau, const double2* __restrict__ G,
@@ -239,8 +248,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int s = kb % STAGES;
         if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, abort_p)) break;
         uint8_t* st = stage_ptr(s);
-        mbar_expect_tx(&full[s], STAGE_BYTES);
-        for (int q = 0; q < S; ++q) {
+        mbar_expect_tx(&full[s], SE * (A_TILE + X_TILE));
+        for (int q = 0; q < SE; ++q) {
           tma_load_4d(st + q * A_TILE, &amap, &full[s], kb * BK, mt * BM, site, q);
           tma_load_4d(st + S * A_TILE + q * X_TILE, &xmap, &full[s], kb * BK, nt * BN, site, q);
         }
@@ -260,14 +269,12 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int k16 = 0; k16 < BK / 16; ++k16) {
 #pragma unroll
-          for (int p = 0; p < NPROD; ++p) {
-            constexpr int dummy = 0;
-            (void)dummy;
-            const Prod pr = prod_of(p);
+          for (int p = 0; p < SE * (SE + 1) / 2; ++p) {
+            const Prod pr = prod_of<SE>(p);
             const uint64_t ad = sdesc_sw64(base + (pr.s - 1) * A_TILE + k16 * 32);
             const uint64_t xd = sdesc_sw64(base + S * A_TILE + (pr.t - 1) * X_TILE + k16 * 32);
             // the first product of each accumulator at the first k step overwrites it
-            const bool first = (kb == 0 && k16 == 0 && (p == 0 || prod_of(p - 1).acc != pr.acc));
+            const bool first = (kb == 0 && k16 == 0 && (p == 0 || prod_of<SE>(p - 1).acc != pr.acc));
             mma<0>(tmem + (uint32_t)(pr.acc * BN), ad, xd, IDESC, first ? 0u : 1u);
           }
         }
@@ -404,7 +411,8 @@ void oz_invalidate(dyson_ctx* c) {
   if (c->oz) static_cast<OzState*>(c->oz)->a_ready = false;
 }
 
-int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32) {
+int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, double tol) {
+  const bool short_split = tol >= SHORT_TOL;
   OzState* st = state(c);
   const int Nr = c->Nr, Nc = c->Nc, N2 = 2 * Nc;
   int rc;
@@ -434,16 +442,23 @@ int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32) {
     st->xmap_ncol = ncol;
   }
   if (!st->smem_set) {
-    DY_CUDA(c, cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    DY_CUDA(c, cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    DY_CUDA(c, cudaFuncSetAttribute(k_oz_gemm<S_SHORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     st->smem_set = true;
   }
   size_t warps = (size_t)Nr * ncol;
   k_oz_xprep<<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(G, c->dJ, c->d_nbr, c->d_nbond, Nr, c->Nt, Nc,
-                                                                ncol, st->xslices, st->tau);
+                                                                ncol, short_split ? S_SHORT : S, st->xslices,
+                                                                st->tau);
   dim3 grid(N2 / BM, (ncol + BN - 1) / BN, Nr);
-  k_oz_gemm<<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
-                                                      c->d_src_site, c->d_src_time, Nc, ncol, gs, r32, c->d_norm,
-                                                      st->d_err);
+  if (short_split)
+    k_oz_gemm<S_SHORT><<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
+                                                                 c->d_src_site, c->d_src_time, Nc, ncol, gs, r32,
+                                                                 c->d_norm, st->d_err);
+  else
+    k_oz_gemm<S><<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
+                                                           c->d_src_site, c->d_src_time, Nc, ncol, gs, r32,
+                                                           c->d_norm, st->d_err);
   c->launches += 2;
   DY_CUDA(c, cudaGetLastError());
   return DYSON_OK;

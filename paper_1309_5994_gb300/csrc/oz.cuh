@@ -8,8 +8,9 @@ bool oz_supported(dyson_ctx* c);
 size_t oz_bytes_per_element();
 // forget the Lambda slices (after dyson_build_sigma)
 void oz_invalidate(dyson_ctx* c);
-// r32 = B + K G - G (FP32 planar output, values accurate to ~2^-43 of |K||G|); c->d_norm[q] = max |r|
-int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32);
+// r32 = B + K G - G (FP32 planar output, values accurate to ~2^-43 of |K||G|, ~2^-33 when tol >= 1e-8,
+// where the first five of the seven slices are used); c->d_norm[q] = max |r|
+int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, double tol);
 // DYSON_ERR_TIMEOUT if a bounded pipeline wait expired (clears the flag)
 int oz_check_error(dyson_ctx* c);
 void oz_release(dyson_ctx* c);

@@ -106,6 +106,27 @@ def test_tensor_core_path_matches_dense(torch_cuda, lib, kw):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
 
+@pytest.mark.parametrize("tol", [1e-8, 1e-6])
+def test_short_slice_residual_at_loose_tolerances(torch_cuda, lib, tol):
+    """Tolerances of 1e-8 and looser compute the FP64-accurate residual from the first five
+    operand slices (15 products): the residual the solve reports must still be the true
+    residual of the returned G, re-evaluated in complex128 by the oracle, to 2 % of the tolerance."""
+    p = wl.random_tables(wl.small(**TC_CASES[0]), seed=31, rel=0.2)
+    S = dyson.setup(p)
+    sources = list(range(p.Nr))
+    s = _solver(p)
+    s.profile(True)
+    got, res = _solve(torch_cuda, s, p, sources, 1, tol=tol)
+    assert s.profile_query(4)[0] == res.report["refinements"] > 0
+    B = dyson.rhs_block_columns(S, sources)
+    G = np.concatenate([got[q] for q in range(len(sources))], axis=2)
+    D = G - B - dyson.apply_K(S, G)
+    R = np.maximum(np.abs(D.real), np.abs(D.imag))       # the tensor-core path's norm: the larger component
+    true = max(R[:, :, q * p.Nc:(q + 1) * p.Nc].max() / np.abs(B[:, :, q * p.Nc:(q + 1) * p.Nc]).max()
+               for q in range(len(sources)))
+    assert true <= tol and abs(res.report["residual"] - true) <= 0.02 * tol
+
+
 def test_pair_kernel_ragged_column_tiles(torch_cuda, lib):
     """Nc = 128 with the CTA-pair sweep selected.  Three block columns make 384
     vector columns: the last 256-column tile has its odd CTA's half wholly past the end."""
