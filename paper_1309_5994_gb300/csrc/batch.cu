@@ -40,10 +40,11 @@ struct BatchCheck {                 // what the check kernel reads per instance
 
 struct BatchStop {                  // inner-series stopping state per instance
   double best, peak, last;
+  double target;                     // update at which this refinement's series stops
   int since_best, sweeps, diverged, pad;
 };
 
-// Stopping rule of the inner series (kInnerTarget, kStallDrop, kStallSweeps) per
+// Stopping rule of the inner series (the refinement's target, kStallDrop, kStallSweeps) per
 // active instance; clears the norm words for the next sweep and counts the
 // instances still active.  One block.
 __global__ void k_batch_check(const BatchCheck* __restrict__ chk, int n, int* __restrict__ active,
@@ -82,8 +83,8 @@ __global__ void k_batch_check(const BatchCheck* __restrict__ chk, int n, int* __
       } else {
         S.since_best += 1;
       }
-      stop = upd <= kInnerTarget || (S.since_best >= kStallSweeps && S.best < kStallDrop * S.peak) ||
-             S.sweeps >= C.max_sweeps;
+      stop = (upd <= S.target && (upd < S.peak || upd == 0.0)) ||
+             (S.since_best >= kStallSweeps && S.best < kStallDrop * S.peak) || S.sweeps >= C.max_sweeps;
     }
     st[k] = S;
     if (stop) active[k] = 0;
@@ -341,6 +342,7 @@ int dyson_batch_solve(dyson_batch* b, const int32_t* const* src, const int32_t* 
       b->h_active[k] = X.done ? 0 : 1;
       std::memset(&b->h_stop[k], 0, sizeof(BatchStop));
       b->h_stop[k].best = std::numeric_limits<double>::infinity();
+      b->h_stop[k].target = inner_target(kInnerTarget, tol, X.prev_res);
       if (X.done) continue;
       ++n_live;
       const size_t n32 = (size_t)X.c->Nr * X.ncol * 2 * X.c->Nc;

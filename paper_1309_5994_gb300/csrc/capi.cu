@@ -169,7 +169,7 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
 int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float* da, float* db, int max_sweeps,
                 const std::vector<double>& rref, float** dres, dyson_report* rep, double* peak_out,
                 double abort_peak = std::numeric_limits<double>::infinity(), const int* act = nullptr,
-                bool* exhausted = nullptr) {
+                bool* exhausted = nullptr, double target = kInnerTarget) {
   if (exhausted) *exhausted = false;
   const int ng = ncol / gs;
   const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
@@ -217,7 +217,7 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
       if (peak_out) *peak_out = peak;
       return DYSON_ERR_DIVERGED;                           // the caller switches to GMRES
     }
-    if (upd <= kInnerTarget) break;
+    if (upd <= target && (upd < peak || upd == 0.0)) break;   // on the decay, not before the peak
     if (since_best >= kStallSweeps && best < kStallDrop * peak) break;
     if (sweep == max_sweeps && exhausted) *exhausted = true;
   }
@@ -329,7 +329,7 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
   for (int ref = 0; ref < c->max_refinements; ++ref) {
     float* d = nullptr;
     if (gmres) {
-      rc = gmres_inner_solve(c, ncol, r32, da, max_sweeps, kGmresTarget, rep, mv);
+      rc = gmres_inner_solve(c, ncol, r32, da, max_sweeps, inner_target(kGmresTarget, tol, prev_res), rep, mv);
       d = da;
       rep->inner_gmres = 1;
     } else {
@@ -340,7 +340,8 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
                            : nullptr;
       bool exhausted = false;
       rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep, &peak,
-                       may_switch ? kSeriesPeakMax : std::numeric_limits<double>::infinity(), act, &exhausted);
+                       may_switch ? kSeriesPeakMax : std::numeric_limits<double>::infinity(), act, &exhausted,
+                       inner_target(kInnerTarget, tol, prev_res));
       if (rc == DYSON_ERR_DIVERGED && may_switch) {
         gmres = true;                                    // redo this refinement with GMRES
         --ref;

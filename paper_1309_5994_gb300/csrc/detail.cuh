@@ -32,6 +32,18 @@ constexpr double kDivergedF64 = 4503599627370496.0;
 // sits kStallDrop below its peak and has not improved for kStallSweeps sweeps
 // (improvement counted from the latest peak, never during the growth).
 constexpr double kInnerTarget = 4e-7;
+// A refinement only has to take the residual from its previous value r_prev to the
+// tolerance: its inner solve stops at an update of kInnerSlack * tol / r_prev (at
+// most kInnerCap; never below kInnerTarget or kGmresTarget).  The update overstates
+// nothing by more than a few times, so the slack of 10 keeps the next residual
+// below the tolerance.
+constexpr double kInnerSlack = 0.1;
+constexpr double kInnerCap = 1e-2;
+inline double inner_target(double floor_target, double tol, double prev_res) {
+  if (!(prev_res < 1e300)) return floor_target;
+  const double t = kInnerSlack * tol / prev_res;
+  return t > kInnerCap ? kInnerCap : (t > floor_target ? t : floor_target);
+}
 constexpr double kStallDrop = 1e-4;
 constexpr int kStallSweeps = 4;
 
