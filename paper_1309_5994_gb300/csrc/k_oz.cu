@@ -36,9 +36,14 @@ constexpr double SHORT_TOL = 1e-8;
 constexpr int BM = 128, BN = 96, BK = 32;                 // BK bf16 = 64-byte rows (64-byte swizzle)
 constexpr int A_TILE = BM * BK * 2;                       // 8 KB per A slice tile
 constexpr int X_TILE = BN * BK * 2;                       // 6 KB per X slice tile
-constexpr int STAGE_BYTES = S * (A_TILE + X_TILE);        // S A slices + S X slices (98 KB)
-constexpr int STAGES = 2;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+// pipeline of one slice count: a stage holds SE A slices and SE X slices (70 KB for
+// five, 98 KB for seven); as many stages as fit (three for five slices, two for seven)
+template <int SE>
+struct OzPipe {
+  static constexpr int STAGE_BYTES = SE * (A_TILE + X_TILE);
+  static constexpr int STAGES = 3 * STAGE_BYTES + 1024 <= 227 * 1024 ? 3 : 2;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+};
 constexpr int THREADS = 256;
 constexpr int NACC = 5;                                    // diagonals {2}, {3}, {4}, {5}, {6, 7, 8}
 constexpr uint32_t TMEM_COLS = 512;                        // 5 accumulators x 96 columns
@@ -217,6 +222,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int STAGES = OzPipe<SE>::STAGES, STAGE_BYTES = OzPipe<SE>::STAGE_BYTES;
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full;
   __shared__ uint32_t tmem_holder;
   __shared__ int abort_flag;
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_expect_tx(&full[s], SE * (A_TILE + X_TILE));
         for (int q = 0; q < SE; ++q) {
           tma_load_4d(st + q * A_TILE, &amap, &full[s], kb * BK, mt * BM, site, q);
-          tma_load_4d(st + S * A_TILE + q * X_TILE, &xmap, &full[s], kb * BK, nt * BN, site, q);
+          tma_load_4d(st + SE * A_TILE + q * X_TILE, &xmap, &full[s], kb * BK, nt * BN, site, q);
         }
         issued = kb + 1;
       }
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int p = 0; p < SE * (SE + 1) / 2; ++p) {
             const Prod pr = prod_of<SE>(p);
             const uint64_t ad = sdesc_sw64(base + (pr.s - 1) * A_TILE + k16 * 32);
-            const uint64_t xd = sdesc_sw64(base + S * A_TILE + (pr.t - 1) * X_TILE + k16 * 32);
+            const uint64_t xd = sdesc_sw64(base + SE * A_TILE + (pr.t - 1) * X_TILE + k16 * 32);
             // the first product of each accumulator at the first k step overwrites it
             const bool first = (kb == 0 && k16 == 0 && (p == 0 || prod_of<SE>(p - 1).acc != pr.acc));
             mma<0>(tmem + (uint32_t)(pr.acc * BN), ad, xd, IDESC, first ? 0u : 1u);
@@ -442,8 +448,10 @@ int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, do
     st->xmap_ncol = ncol;
   }
   if (!st->smem_set) {
-    DY_CUDA(c, cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    DY_CUDA(c, cudaFuncSetAttribute(k_oz_gemm<S_SHORT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    DY_CUDA(c, cudaFuncSetAttribute(k_oz_gemm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    OzPipe<S>::SMEM_BYTES));
+    DY_CUDA(c, cudaFuncSetAttribute(k_oz_gemm<S_SHORT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    OzPipe<S_SHORT>::SMEM_BYTES));
     st->smem_set = true;
   }
   size_t warps = (size_t)Nr * ncol;
@@ -452,11 +460,11 @@ int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, do
                                                                 st->tau);
   dim3 grid(N2 / BM, (ncol + BN - 1) / BN, Nr);
   if (short_split)
-    k_oz_gemm<S_SHORT><<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
+    k_oz_gemm<S_SHORT><<<grid, THREADS, OzPipe<S_SHORT>::SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
                                                                  c->d_src_site, c->d_src_time, Nc, ncol, gs, r32,
                                                                  c->d_norm, st->d_err);
   else
-    k_oz_gemm<S><<<grid, THREADS, SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
+    k_oz_gemm<S><<<grid, THREADS, OzPipe<S>::SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
                                                            c->d_src_site, c->d_src_time, Nc, ncol, gs, r32,
                                                            c->d_norm, st->d_err);
   c->launches += 2;
