@@ -20,7 +20,10 @@
 // tolerance).
 //
 // Kernels: k_oz_aprep (once per Lambda), k_oz_xprep (gather + scale + slice of X
-// per residual), k_oz_gemm (TMA + tcgen05.mma kind::f16 + FP64 epilogue).
+// per residual), k_oz_gemm (persistent: TMA + tcgen05.mma kind::f16 into two
+// accumulator sets + FP64 epilogue of the previous tile).
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
@@ -33,22 +36,24 @@ namespace {
 constexpr int S = 7;                                      // slices stored
 constexpr int S_SHORT = 5;                                 // slices used for tolerances >= 1e-8
 constexpr double SHORT_TOL = 1e-8;
-constexpr int BM = 128, BN = 96, BK = 32;                 // BK bf16 = 64-byte rows (64-byte swizzle)
+constexpr int BM = 128, BN = 48, BK = 32;                 // BK bf16 = 64-byte rows (64-byte swizzle)
 constexpr int A_TILE = BM * BK * 2;                       // 8 KB per A slice tile
-constexpr int X_TILE = BN * BK * 2;                       // 6 KB per X slice tile
-// pipeline of one slice count: a stage holds SE A slices and SE X slices (70 KB for
-// five, 98 KB for seven); as many stages as fit (three for five slices, two for seven)
+constexpr int X_TILE = BN * BK * 2;                       // 3 KB per X slice tile
+// pipeline of one slice count: a stage holds SE A slices and SE X slices (55 KB for
+// five, 77 KB for seven); as many stages as fit, at most four
 template <int SE>
 struct OzPipe {
   static constexpr int STAGE_BYTES = SE * (A_TILE + X_TILE);
-  static constexpr int STAGES = 3 * STAGE_BYTES + 1024 <= 227 * 1024 ? 3 : 2;
+  static constexpr int FIT = (227 * 1024 - 1024) / STAGE_BYTES;
+  static constexpr int STAGES = FIT > 4 ? 4 : FIT;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 };
 constexpr int THREADS = 256;
 constexpr int NACC = 5;                                    // diagonals {2}, {3}, {4}, {5}, {6, 7, 8}
-constexpr uint32_t TMEM_COLS = 512;                        // 5 accumulators x 96 columns
+constexpr uint32_t ACC_COLS = NACC * BN;                   // one tile's accumulators: 240 columns
+constexpr uint32_t TMEM_COLS = 512;                        // two tiles' accumulators (double-buffered)
 
-// kind::f16, D = F32, A = B = BF16, K-major, M = 128, N = 96
+// kind::f16, D = F32, A = B = BF16, K-major, M = 128, N = 48
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
@@ -64,6 +69,7 @@ struct OzState {
   const void* xmap_ptr = nullptr;
   int xmap_ncol = -1;
   int* d_err = nullptr;
+  int num_sms = 1;
   bool smem_set = false;
 };
 
@@ -212,30 +218,40 @@ __host__ __device__ constexpr Prod prod_of(int p) {
   return Prod{0, 0, 0};
 }
 
+// Persistent: one CTA per SM walks the 128 x 48 output tiles (row tile fastest, then
+// column tile, then site).  Warp roles: warp 0 TMA loads (SE A slices and SE X slices
+// per k-block), warp 1 one thread issuing the slice products into one of two
+// accumulator sets in TMEM, warps 4-7 the epilogue of the previous tile.  Every
+// mbarrier wait is bounded; on expiry the CTA raises the error flag and drains.
 template <int SE>
 __global__ void __launch_bounds__(THREADS, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap xmap,
               const double* __restrict__ sigma, const double* __restrict__ tau, const double2* __restrict__ G,
               const double2* __restrict__ lam, const int* __restrict__ src_site, const int* __restrict__ src_time,
-              int Nc, int ncol, int gs, float* __restrict__ r32, unsigned long long* __restrict__ norm,
+              int Nr, int Nc, int ncol, int gs, float* __restrict__ r32, unsigned long long* __restrict__ norm,
               int* __restrict__ err) {
   using namespace ptx;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int STAGES = OzPipe<SE>::STAGES, STAGE_BYTES = OzPipe<SE>::STAGE_BYTES;
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tmem_holder;
   __shared__ int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mt = blockIdx.x, nt = blockIdx.y, site = blockIdx.z;
   const int N2 = 2 * Nc, KB = N2 / BK;
+  const int MT = N2 / BM, NT = (ncol + BN - 1) / BN;
+  const int tiles = MT * NT * Nr;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&acc_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    mbar_init(&drain, 1);
     abort_flag = 0;
     fence_barrier_init();
   }
@@ -249,62 +265,90 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % STAGES;
-        if (kb >= STAGES && !mbar_wait(&empty[s], ((kb / STAGES) - 1) & 1, abort_p)) break;
-        uint8_t* st = stage_ptr(s);
-        mbar_expect_tx(&full[s], SE * (A_TILE + X_TILE));
-        for (int q = 0; q < SE; ++q) {
-          tma_load_4d(st + q * A_TILE, &amap, &full[s], kb * BK, mt * BM, site, q);
-          tma_load_4d(st + SE * A_TILE + q * X_TILE, &xmap, &full[s], kb * BK, nt * BN, site, q);
+      // ---------------- TMA producer ----------------
+      int g = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int mt = tile % MT, nt = (tile / MT) % NT, site = tile / (MT * NT);
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1, abort_p)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = stage_ptr(s);
+          mbar_expect_tx(&full[s], SE * (A_TILE + X_TILE));
+          for (int q = 0; q < SE; ++q) {
+            tma_load_4d(st + q * A_TILE, &amap, &full[s], kb * BK, mt * BM, site, q);
+            tma_load_4d(st + SE * A_TILE + q * X_TILE, &xmap, &full[s], kb * BK, nt * BN, site, q);
+          }
         }
-        issued = kb + 1;
       }
-      for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
-        mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, abort_p, false);
+      // let every copy this thread issued land before the CTA can exit
+      for (int q = g > STAGES ? g - STAGES : 0; q < g; ++q)
+        mbar_wait(&full[q % STAGES], (q / STAGES) & 1, abort_p, false);
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      bool any = false;
-      for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb % STAGES;
-        if (!mbar_wait(&full[s], (kb / STAGES) & 1, abort_p)) break;
+      // ---------------- MMA issuer ----------------
+      int g = 0, t = 0;
+      bool ok = true, any = false;
+      for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        const int buf = t & 1;
+        if (t >= 2 && !mbar_wait(&acc_empty[buf], ((t >> 1) - 1) & 1, abort_p)) break;
+        ++t;
         tc_fence_after();
-        const uint32_t base = smem_u32(stage_ptr(s));
-#pragma unroll
-        for (int k16 = 0; k16 < BK / 16; ++k16) {
-#pragma unroll
-          for (int p = 0; p < SE * (SE + 1) / 2; ++p) {
-            const Prod pr = prod_of<SE>(p);
-            const uint64_t ad = sdesc_sw64(base + (pr.s - 1) * A_TILE + k16 * 32);
-            const uint64_t xd = sdesc_sw64(base + SE * A_TILE + (pr.t - 1) * X_TILE + k16 * 32);
-            // the first product of each accumulator at the first k step overwrites it
-            const bool first = (kb == 0 && k16 == 0 && (p == 0 || prod_of<SE>(p - 1).acc != pr.acc));
-            mma<0>(tmem + (uint32_t)(pr.acc * BN), ad, xd, IDESC, first ? 0u : 1u);
+        const uint32_t dacc = tmem + (uint32_t)(buf * ACC_COLS);
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (!mbar_wait(&full[s], (g / STAGES) & 1, abort_p)) {
+            ok = false;
+            break;
           }
+          tc_fence_after();
+          const uint32_t base = smem_u32(stage_ptr(s));
+#pragma unroll
+          for (int k16 = 0; k16 < BK / 16; ++k16) {
+#pragma unroll
+            for (int p = 0; p < SE * (SE + 1) / 2; ++p) {
+              const Prod pr = prod_of<SE>(p);
+              const uint64_t ad = sdesc_sw64(base + (pr.s - 1) * A_TILE + k16 * 32);
+              const uint64_t xd = sdesc_sw64(base + SE * A_TILE + (pr.t - 1) * X_TILE + k16 * 32);
+              // the first product of each accumulator at the first k step overwrites it
+              const bool first = (kb == 0 && k16 == 0 && (p == 0 || prod_of<SE>(p - 1).acc != pr.acc));
+              mma<0>(dacc + (uint32_t)(pr.acc * BN), ad, xd, IDESC, first ? 0u : 1u);
+            }
+          }
+          mma_commit(&empty[s]);
+          any = true;
         }
-        mma_commit(&empty[s]);
-        any = true;
+        if (ok) mma_commit(&acc_full[buf]);
       }
       if (any) {
-        mma_commit(&acc_full);
-        mbar_wait(&acc_full, 0, abort_p, false);
+        mma_commit(&drain);                               // all MMAs of this thread completed
+        mbar_wait(&drain, 0, abort_p, false);
       }
     }
   } else if (warp >= 4) {
-    bool go = mbar_wait(&acc_full, 0, abort_p);
-    go = __all_sync(0xffffffffu, go);
-    if (go) {
+    // ---------------- epilogue ----------------
+    const int q4 = warp - 4;                             // TMEM lane quarter
+    int t = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      const int mt = tile % MT, nt = (tile / MT) % NT, site = tile / (MT * NT);
+      const int buf = t & 1;
+      bool go = mbar_wait(&acc_full[buf], (t >> 1) & 1, abort_p);
+      ++t;
+      go = __all_sync(0xffffffffu, go);                 // tcgen05.ld below is warp-collective
+      if (!go) break;
       tc_fence_after();
-      const int q4 = warp - 4;
       const int m = mt * BM + q4 * 32 + lane;            // planar row: part m / Nc, contour row z = m % Nc
       const int z = m % Nc, part = m / Nc;
       const double sg = sigma[(size_t)site * N2 + m] * ldexp(1.0, -FIX);   // row scale / fixed-point unit
+      const uint32_t tacc = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS);
       int qcur = (nt * BN) / gs;
       float runmax = 0.f;
-      for (int c = 0; c < BN / 32; ++c) {
-        const int n0 = nt * BN + c * 32;
+      for (int c = 0; c < BN / 16; ++c) {
+        const int n0 = nt * BN + c * 16;
         if (n0 >= ncol) break;                          // warp-uniform; ncol and gs are multiples of 32
         const int q = n0 / gs;
         if (q != qcur) {
@@ -317,27 +361,27 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         // the accumulators hold integer multiples of 2^{-7d}: sum them exactly in
         // 2^-FIX fixed point (int64), then convert once
-        long long acc[32];
-        uint32_t rr[32];
+        long long acc[16];
+        uint32_t rr[16];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = 0;
+        for (int j = 0; j < 16; ++j) acc[j] = 0;
 #pragma unroll
         for (int a = 0; a < NACC; ++a) {
-          tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(a * BN + c * 32), rr);
+          tmem_ld16(tacc + (uint32_t)(a * BN + c * 16), rr);
           tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[j] += f32_to_fixed(__uint_as_float(rr[j]));
+          for (int j = 0; j < 16; ++j) acc[j] += f32_to_fixed(__uint_as_float(rr[j]));
         }
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < 16; ++j) {
           const int n = n0 + j;
-          const double2 g = G[((size_t)site * ncol + n) * Nc + z];
+          const double2 gv = G[((size_t)site * ncol + n) * Nc + z];
           double b = 0.0;
           if (src_site[n] == site) {                    // B = Lambda_s e_{z'} on the source site
             const double2 lv = lam[((size_t)site * Nc + z) * Nc + src_time[n]];
             b = part ? lv.y : lv.x;
           }
-          const double rv = b + (double)acc[j] * (sg * tau[(size_t)site * ncol + n]) - (part ? g.y : g.x);
+          const double rv = b + (double)acc[j] * (sg * tau[(size_t)site * ncol + n]) - (part ? gv.y : gv.x);
           r32[((size_t)site * ncol + n) * N2 + m] = (float)rv;
           float d = fabsf((float)rv);
           d = (d == d) ? d : __int_as_float(0x7f800000);
@@ -348,6 +392,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
       if (lane == 0) atomicMax(norm + qcur, (unsigned long long)__double_as_longlong((double)mm));
+      // this accumulator set may be overwritten by the MMAs of tile t + 2
+      tc_fence_before();
+      mbar_arrive(&acc_empty[buf]);
     }
   }
 
@@ -425,6 +472,7 @@ int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, do
   if (!st->d_err) {
     DY_CUDA(c, cudaMalloc(&st->d_err, sizeof(int)));
     DY_CUDA(c, cudaMemsetAsync(st->d_err, 0, sizeof(int), c->stream));
+    DY_CUDA(c, cudaDeviceGetAttribute(&st->num_sms, cudaDevAttrMultiProcessorCount, c->device));
   }
   if (!st->a_ready) {
     size_t abytes = (size_t)S * Nr * N2 * N2 * 2;
@@ -458,15 +506,16 @@ int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, do
   k_oz_xprep<<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(G, c->dJ, c->d_nbr, c->d_nbond, Nr, c->Nt, Nc,
                                                                 ncol, short_split ? S_SHORT : S, st->xslices,
                                                                 st->tau);
-  dim3 grid(N2 / BM, (ncol + BN - 1) / BN, Nr);
+  const long long tiles = (long long)(N2 / BM) * ((ncol + BN - 1) / BN) * Nr;
+  const int grid = (int)std::min<long long>(tiles, st->num_sms);
   if (short_split)
-    k_oz_gemm<S_SHORT><<<grid, THREADS, OzPipe<S_SHORT>::SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
-                                                                 c->d_src_site, c->d_src_time, Nc, ncol, gs, r32,
-                                                                 c->d_norm, st->d_err);
+    k_oz_gemm<S_SHORT><<<grid, THREADS, OzPipe<S_SHORT>::SMEM_BYTES, c->stream>>>(
+        st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam, c->d_src_site, c->d_src_time, Nr, Nc, ncol, gs, r32,
+        c->d_norm, st->d_err);
   else
-    k_oz_gemm<S><<<grid, THREADS, OzPipe<S>::SMEM_BYTES, c->stream>>>(st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam,
-                                                           c->d_src_site, c->d_src_time, Nc, ncol, gs, r32,
-                                                           c->d_norm, st->d_err);
+    k_oz_gemm<S><<<grid, THREADS, OzPipe<S>::SMEM_BYTES, c->stream>>>(
+        st->amap, st->xmap, st->sigma, st->tau, G, c->d_lam, c->d_src_site, c->d_src_time, Nr, Nc, ncol, gs, r32,
+        c->d_norm, st->d_err);
   c->launches += 2;
   DY_CUDA(c, cudaGetLastError());
   return DYSON_OK;
