@@ -48,7 +48,8 @@ struct OzPipe {
   static constexpr int STAGES = FIT > 4 ? 4 : FIT;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 };
-constexpr int THREADS = 256;
+constexpr int THREADS = 384;                               // warps 4-11: epilogue, two per TMEM lane quarter
+constexpr int EPI_CHUNK = 8;                               // accumulator columns per tcgen05.ld
 constexpr int NACC = 5;                                    // diagonals {2}, {3}, {4}, {5}, {6, 7, 8}
 constexpr uint32_t ACC_COLS = NACC * BN;                   // one tile's accumulators: 240 columns
 constexpr uint32_t TMEM_COLS = 512;                        // two tiles' accumulators (double-buffered)
@@ -106,18 +107,21 @@ __device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_
   }
 }
 
-// rint(f * 2^FIX) for an FP32 accumulator value, by integer arithmetic on its bits
-__device__ __forceinline__ long long f32_to_fixed(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const int e = (int)((b >> 23) & 0xFF);
-  if (e == 0) return 0;                                    // zero (denormals are far below 2^-FIX)
-  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
-  const int sh = e - 150 + FIX;                            // f 2^FIX = m 2^sh
-  long long v;
-  if (sh >= 0) v = m << sh;                                // exact: |f| < 2^10 keeps this below 2^63
-  else if (sh > -40) v = (m + (1LL << (-sh - 1))) >> (-sh);
-  else v = 0;
-  return (b >> 31) ? -v : v;
+// Accumulator A of the slice products holds, for A < NACC - 1, sum q_s q_t 2^{-7 d} over
+// the diagonal d = A + 2 exactly: an integer N below 2^24 in units of 2^{-7 d}, moved to
+// the 2^-FIX fixed point by one exact scaling, an exact int32 conversion and a shift.
+// The last accumulator (diagonals >= NACC + 1, rounded in FP32) is scaled by 2^FIX and
+// rounded to the nearest integer in 64 bits (its magnitude stays below 2^-18 for
+// K <= 512), so nothing but the part below 2^-FIX is lost.
+template <int A>
+__device__ __forceinline__ long long acc_to_fixed(float v) {
+  if constexpr (A < NACC - 1) {
+    constexpr int d = A + 2;
+    const int N = __float2int_rn(v * __int_as_float((127 + 7 * d) << 23));   // v * 2^{7 d}, exact
+    return (long long)N << (FIX - 7 * d);
+  } else {
+    return __float2ll_rn(v * __int_as_float((127 + FIX) << 23));            // v * 2^FIX
+  }
 }
 
 __device__ __forceinline__ double emb_value(const double2* lrow, int k, int part, int Nc, int Nt, int Nm, double dt,
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 128);
+      mbar_init(&acc_empty[b], 256);                   // 8 epilogue warps
     }
     mbar_init(&drain, 1);
     abort_flag = 0;
@@ -330,8 +334,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp >= 4) {
-    // ---------------- epilogue ----------------
-    const int q4 = warp - 4;                             // TMEM lane quarter
+    // ---------------- epilogue: warps 4-11, two per TMEM lane quarter ----------------
+    const int q4 = warp & 3;                             // TMEM lane quarter (a warp reads lanes 32 (warp % 4) ..)
+    const int half = (warp - 4) >> 2;                    // which half of the tile's column chunks
     int t = 0;
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
       const int mt = tile % MT, nt = (tile / MT) % NT, site = tile / (MT * NT);
@@ -345,10 +350,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int z = m % Nc, part = m / Nc;
       const double sg = sigma[(size_t)site * N2 + m] * ldexp(1.0, -FIX);   // row scale / fixed-point unit
       const uint32_t tacc = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS);
-      int qcur = (nt * BN) / gs;
+      constexpr int CHUNKS = BN / EPI_CHUNK, PER_HALF = CHUNKS / 2;
+      int qcur = (nt * BN + half * PER_HALF * EPI_CHUNK) / gs;
       float runmax = 0.f;
-      for (int c = 0; c < BN / 16; ++c) {
-        const int n0 = nt * BN + c * 16;
+      for (int cc = 0; cc < PER_HALF; ++cc) {
+        const int c = half * PER_HALF + cc;
+        const int n0 = nt * BN + c * EPI_CHUNK;
         if (n0 >= ncol) break;                          // warp-uniform; ncol and gs are multiples of 32
         const int q = n0 / gs;
         if (q != qcur) {
@@ -361,19 +368,19 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         // the accumulators hold integer multiples of 2^{-7d}: sum them exactly in
         // 2^-FIX fixed point (int64), then convert once
-        long long acc[16];
-        uint32_t rr[16];
+        uint32_t r0[EPI_CHUNK], r1[EPI_CHUNK], r2[EPI_CHUNK], r3[EPI_CHUNK], r4[EPI_CHUNK];
+        const uint32_t col = (uint32_t)(c * EPI_CHUNK);
+        tmem_ld8(tacc + col, r0);
+        tmem_ld8(tacc + (uint32_t)BN + col, r1);
+        tmem_ld8(tacc + (uint32_t)(2 * BN) + col, r2);
+        tmem_ld8(tacc + (uint32_t)(3 * BN) + col, r3);
+        tmem_ld8(tacc + (uint32_t)(4 * BN) + col, r4);
+        tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = 0;
-#pragma unroll
-        for (int a = 0; a < NACC; ++a) {
-          tmem_ld16(tacc + (uint32_t)(a * BN + c * 16), rr);
-          tmem_wait_ld();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[j] += f32_to_fixed(__uint_as_float(rr[j]));
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
+        for (int j = 0; j < EPI_CHUNK; ++j) {
+          const long long acc = acc_to_fixed<0>(__uint_as_float(r0[j])) + acc_to_fixed<1>(__uint_as_float(r1[j])) +
+                                acc_to_fixed<2>(__uint_as_float(r2[j])) + acc_to_fixed<3>(__uint_as_float(r3[j])) +
+                                acc_to_fixed<4>(__uint_as_float(r4[j]));
           const int n = n0 + j;
           const double2 gv = G[((size_t)site * ncol + n) * Nc + z];
           double b = 0.0;
@@ -381,7 +388,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const double2 lv = lam[((size_t)site * Nc + z) * Nc + src_time[n]];
             b = part ? lv.y : lv.x;
           }
-          const double rv = b + (double)acc[j] * (sg * tau[(size_t)site * ncol + n]) - (part ? gv.y : gv.x);
+          const double rv = b + (double)acc * (sg * tau[(size_t)site * ncol + n]) - (part ? gv.y : gv.x);
           r32[((size_t)site * ncol + n) * N2 + m] = (float)rv;
           float d = fabsf((float)rv);
           d = (d == d) ? d : __int_as_float(0x7f800000);
