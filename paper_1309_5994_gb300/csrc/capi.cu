@@ -261,7 +261,7 @@ const int* support_table(dyson_ctx* c, int ncol) {
     int last = -1;
     for (int v = t * TC_TILE_COLS; v < v1; ++v) {
       const int s = c->h_src_site[v];
-      if (s == last) continue;
+      if (s == last || s < 0) continue;                  // padding columns (site -1) stay zero
       last = s;
       const int sx = s % c->Lx, sy = s / c->Lx;
       for (int i = 0; i < c->Nr; ++i) {
