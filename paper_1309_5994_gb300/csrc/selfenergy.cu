@@ -606,27 +606,26 @@ int ensure_state(dyson_ctx* c) {
     c->se = nullptr;
   }
   st = new SeState();
-  c->se = st;
   st->Nr = c->Nr;
   st->Nc = c->Nc;
   const size_t blk = (size_t)c->Nr * c->Nc * c->Nc * sizeof(double2);
+  bool ok = true;
   double2** bufs[] = {&st->g0, &st->Sm, &st->FT, &st->conn, &st->w1, &st->w2, &st->St};
-  for (double2** b : bufs) {
-    if (cudaMalloc(b, blk) != cudaSuccess) {
-      cudaGetLastError();
-      return ctx_fail(c, DYSON_ERR_OOM, "self-energy buffers");
-    }
-  }
-  if (cudaMalloc(&st->Q, (size_t)c->Nr * 2 * c->Nc * (2 * c->Nt + 1) * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(&st->tr, (size_t)c->Nr * sizeof(double2)) != cudaSuccess ||
-      cudaMalloc(&st->paths, 256 * PATHS * sizeof(uint32_t)) != cudaSuccess ||
-      cudaMalloc(&st->part, 2 * MIX_BLOCKS * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&st->err, (size_t)c->Nr * sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return ctx_fail(c, DYSON_ERR_OOM, "self-energy tables");
-  }
+  for (double2** b : bufs) ok = ok && cudaMalloc(b, blk) == cudaSuccess;
+  ok = ok && cudaMalloc(&st->Q, (size_t)c->Nr * 2 * c->Nc * (2 * c->Nt + 1) * sizeof(double2)) == cudaSuccess &&
+       cudaMalloc(&st->tr, (size_t)c->Nr * sizeof(double2)) == cudaSuccess &&
+       cudaMalloc(&st->paths, 256 * PATHS * sizeof(uint32_t)) == cudaSuccess &&
+       cudaMalloc(&st->part, 2 * MIX_BLOCKS * sizeof(double)) == cudaSuccess &&
+       cudaMalloc(&st->err, (size_t)c->Nr * sizeof(int)) == cudaSuccess;
   const std::vector<uint32_t> tab = path_table();
-  DY_CUDA(c, cudaMemcpy(st->paths, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+  ok = ok && cudaMemcpy(st->paths, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (!ok) {                                             // nothing half-built stays behind
+    cudaGetLastError();
+    free_state(st);
+    delete st;
+    return ctx_fail(c, DYSON_ERR_OOM, "self-energy buffers (7 Nr Nc^2 complex128 and the prefix tables)");
+  }
+  c->se = st;
   return DYSON_OK;
 }
 
