@@ -89,14 +89,10 @@ __device__ __forceinline__ double pow2_scale(double mx) {
 
 constexpr int FIX = 7 * S;                                 // fixed-point bits of a scaled value
 
-// Write the S slices of x / sc (|x| <= sc, sc a power of two).  The value is
-// rounded once to the fixed-point integer V = rint(x 2^FIX / sc) (|V| <= 2^FIX),
-// then cut into signed 7-bit digits with integer shifts: slice s holds
-// q_s 2^{-7 s}, q_s = round(V_rem / 2^{7 (S - s)}), |q_1| <= 128, |q_s| <= 64.
-// Only one FP64 multiply and one conversion per value: FP64 is scarce here.
-__device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_bfloat16* dst, size_t slice_stride,
-                                             int nslices = S) {
-  long long V = __double2ll_rn(x * fix_over_sc);
+// Write the S slices of the fixed-point integer V = rint(x 2^FIX / sc) (|x| <= sc, sc a
+// power of two, |V| <= 2^FIX): V is cut into signed 7-bit digits with integer shifts,
+// slice s holds q_s 2^{-7 s}, q_s = round(V_rem / 2^{7 (S - s)}), |q_1| <= 128, |q_s| <= 64.
+__device__ __forceinline__ void write_digits(long long V, __nv_bfloat16* dst, size_t slice_stride, int nslices) {
 #pragma unroll
   for (int s = 1; s <= S; ++s) {
     const int sh = 7 * (S - s);
@@ -105,6 +101,27 @@ __device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_
     const float part = __int2float_rn((int)q) * __int_as_float((127 - 7 * s) << 23);   // q * 2^{-7 s}, exact
     if (s <= nslices) dst[(size_t)(s - 1) * slice_stride] = __float2bfloat16_rn(part);
   }
+}
+
+// the same with V from one FP64 multiply and one conversion (the Lambda slices, built once)
+__device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_bfloat16* dst, size_t slice_stride,
+                                             int nslices = S) {
+  write_digits(__double2ll_rn(x * fix_over_sc), dst, slice_stride, nslices);
+}
+
+// rint(x 2^k) (|x 2^k| <= 2^FIX) by integer arithmetic on the bits of x, ties rounded away
+// from zero: the FP64 pipe is the scarce one in the slicing of X
+__device__ __forceinline__ long long scaled_to_fixed(double x, int k) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0;                                    // zero, or a denormal far below 2^-FIX of the scale
+  const long long M = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  const int sh = E - 1075 + k;                             // x 2^k = M 2^sh
+  long long v;
+  if (sh >= 0) v = M << sh;                                // |x 2^k| <= 2^FIX keeps this below 2^63
+  else if (sh > -63) v = (M + (1ll << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return (b >> 63) ? -v : v;
 }
 
 // Accumulator A of the slice products holds, for A < NACC - 1, sum q_s q_t 2^{-7 d} over
@@ -167,10 +184,12 @@ __global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restri
     nb[q] = nbr[i * 4 + q];
     bd[q] = nbond[i * 4 + q];
   }
-  // gather once into registers (Nc <= 256: at most 8 points per lane)
+  // gather once into registers (Nc <= 256: at most 8 points per lane); the column max is
+  // taken on the bit patterns of |x| (their unsigned order is the order of the values)
   constexpr int PER_LANE = 256 / 32;
+  constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
   double2 x[PER_LANE];
-  double mx = 0.0;
+  unsigned long long mb = 0;
 #pragma unroll
   for (int u = 0; u < PER_LANE; ++u) {
     const int z = lane + 32 * u;
@@ -187,20 +206,23 @@ __global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restri
       }
     }
     x[u] = make_double2(xr, xi);
-    mx = fmax(mx, fmax(fabs(xr), fabs(xi)));
+    const unsigned long long br = (unsigned long long)__double_as_longlong(xr) & ABS;
+    const unsigned long long bi = (unsigned long long)__double_as_longlong(xi) & ABS;
+    mb = max(mb, max(br, bi));
   }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const double sc = pow2_scale(mx);
-  if (lane == 0) tau[w] = sc;
-  const double fix_over_sc = ldexp(1.0, FIX) / sc;
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, mb, o));
+  // scale sc = 2^e >= max |x| (the exponent of frexp), 1 for an all-zero column
+  const int Emx = (int)((mb >> 52) & 0x7FF);
+  const int e = Emx == 0 ? 0 : Emx - 1022;
+  if (lane == 0) tau[w] = __longlong_as_double((long long)(e + 1023) << 52);
   const size_t stride = (size_t)Nr * ncol * N2;
   __nv_bfloat16* dst = xs + w * N2;
 #pragma unroll
   for (int u = 0; u < PER_LANE; ++u) {
     const int z = lane + 32 * u;
     if (z < Nc) {
-      write_slices(x[u].x, fix_over_sc, dst + z, stride, nslices);
-      write_slices(x[u].y, fix_over_sc, dst + Nc + z, stride, nslices);
+      write_digits(scaled_to_fixed(x[u].x, FIX - e), dst + z, stride, nslices);
+      write_digits(scaled_to_fixed(x[u].y, FIX - e), dst + Nc + z, stride, nslices);
     }
   }
 }
