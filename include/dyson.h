@@ -231,6 +231,18 @@ int dyson_local_greens(dyson_ctx* ctx, const int32_t* src_sites, int64_t n_src, 
  * is installed (they differentiate the atomic Lambda). */
 int dyson_selfenergy_step(dyson_ctx* ctx, const double* gloc, double mix, double* sigma_tilde, double* criterion);
 
+/* Mixing of the self-energy steps: depth 0 (the default) is the linear mixing of
+ * Eq. (Sigmamix); depth 1..6 replaces it by Anderson acceleration of the fixed-point
+ * iteration Sigma~ -> Sigma~_new (an addition to the paper, same fixed point): with
+ * the residual f = Sigma~_new - Sigma~ and the differences dF_i, dX_i of the last
+ * depth residuals and iterates, gamma minimises |f - sum_i gamma_i dF_i|_2 and
+ *   Sigma~ <- Sigma~ + mix f - sum_i gamma_i (dX_i + mix dF_i).
+ * The history restarts here and at dyson_build_sigma.  Device memory: 2 depth + 3
+ * more Nr Nc^2 complex128 arrays on the first Anderson step.  INVALID_ARG for a depth
+ * outside 0..6. */
+#define DYSON_SELFENERGY_MAX_ANDERSON 6
+int dyson_selfenergy_set_anderson(dyson_ctx* ctx, int32_t depth);
+
 /* Delta t -> 0 extrapolation (Sec. IV.D).  The same tables computed on n_grids
  * contours whose steps are h_b = h_0 / m_b (integer divisors, m_0 = 1 < m_1 <
  * ...; the real-time grid of contour b has at least m_b (nt[0] - 1) + 1

@@ -74,7 +74,7 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
            "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune", "dyson_set_symmetry",
            "dyson_adjoint_obs", "dyson_extrapolate_dt", "dyson_set_support_truncation", "dyson_local_greens",
-           "dyson_selfenergy_step"]
+           "dyson_selfenergy_step", "dyson_selfenergy_set_anderson"]
 SYMMETRY_NONE, SYMMETRY_C4V = 0, 1
 INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
 SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
@@ -113,6 +113,7 @@ def load(path: str = _LIB_PATH):
     lib.dyson_local_greens.argtypes = [P, C.POINTER(C.c_int32), C.c_int64, C.c_int, C.c_double, C.c_int32, P,
                                        C.POINTER(Report)]
     lib.dyson_selfenergy_step.argtypes = [P, P, C.c_double, P, C.POINTER(C.c_double)]
+    lib.dyson_selfenergy_set_anderson.argtypes = [P, C.c_int32]
     lib.dyson_launch_count.argtypes = [P]
     lib.dyson_launch_count.restype = C.c_int64
     lib.dyson_solve_block_column_noalloc.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double,
@@ -338,6 +339,10 @@ class Solver:
         st = C.c_void_p(sigma_tilde.data_ptr()) if sigma_tilde is not None else None
         self._check(self.lib.dyson_selfenergy_step(self.h, C.c_void_p(gloc.data_ptr()), mix, st, C.byref(crit)))
         return crit.value
+
+    def set_anderson(self, depth: int):
+        """0: linear mixing of the self-energy steps; 1..6: Anderson acceleration of that depth."""
+        self._check(self.lib.dyson_selfenergy_set_anderson(self.h, depth))
 
     def set_support_truncation(self, enable: bool):
         self._check(self.lib.dyson_set_support_truncation(self.h, 1 if enable else 0))

@@ -507,14 +507,15 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gauss_jordan(double2* __restrict
 // Sigma~ difference and mixing: (sum |dS|^2, max |dS|) per block, dS = Sn - Sm; then Sm = lambda Sn + (1 - lambda) Sm
 constexpr int MIX_BLOCKS = 1024;
 __global__ void k_se_mix(const double2* __restrict__ Sn, double2* __restrict__ Sm, size_t total, double lambda,
-                         double* __restrict__ part) {
+                         double* __restrict__ part, int update) {
   double ss = 0.0, mx = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const double dx = Sn[e].x - Sm[e].x, dy = Sn[e].y - Sm[e].y;
     const double m2 = dx * dx + dy * dy;
     ss += m2;
     mx = fmax(mx, m2);
-    Sm[e] = make_double2(lambda * Sn[e].x + (1.0 - lambda) * Sm[e].x, lambda * Sn[e].y + (1.0 - lambda) * Sm[e].y);
+    if (update)
+      Sm[e] = make_double2(lambda * Sn[e].x + (1.0 - lambda) * Sm[e].x, lambda * Sn[e].y + (1.0 - lambda) * Sm[e].y);
   }
   __shared__ double s1[256], s2[256];
   s1[threadIdx.x] = ss;
@@ -530,6 +531,99 @@ __global__ void k_se_mix(const double2* __restrict__ Sn, double2* __restrict__ S
   if (threadIdx.x == 0) {
     part[2 * blockIdx.x] = s1[0];
     part[2 * blockIdx.x + 1] = s2[0];
+  }
+}
+
+// Anderson acceleration of the loop (an option; the paper mixes linearly): with the
+// residual f = Sigma~_new - Sigma~ of the current iterate and the last m differences
+// dF_i, dX_i of residuals and iterates, gamma minimises |f - sum gamma_i dF_i|_2 and
+//   Sigma~ <- Sigma~ + lambda f - sum_i gamma_i (dX_i + lambda dF_i).
+constexpr int AA_MAX = DYSON_SELFENERGY_MAX_ANDERSON;
+struct AaVecs {
+  const double2* dF[AA_MAX];
+  const double2* dX[AA_MAX];
+  int m;
+};
+
+// f = Sn - Sm; dF_slot = f - f_prev, dX_slot = Sm - x_prev (when have_prev); then f_prev = f, x_prev = Sm
+__global__ void k_aa_push(const double2* __restrict__ Sn, const double2* __restrict__ Sm, double2* __restrict__ f,
+                          double2* __restrict__ fprev, double2* __restrict__ xprev, double2* __restrict__ dF,
+                          double2* __restrict__ dX, int have_prev, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const double2 fe = make_double2(Sn[e].x - Sm[e].x, Sn[e].y - Sm[e].y);
+    const double2 xe = Sm[e];
+    if (have_prev) {
+      dF[e] = make_double2(fe.x - fprev[e].x, fe.y - fprev[e].y);
+      dX[e] = make_double2(xe.x - xprev[e].x, xe.y - xprev[e].y);
+    }
+    f[e] = fe;
+    fprev[e] = fe;
+    xprev[e] = xe;
+  }
+}
+
+// per block: the Gram entries <dF_i, dF_j> (i <= j) and <dF_i, f>, complex, in a fixed order
+__global__ void k_aa_dots(const __grid_constant__ AaVecs v, const double2* __restrict__ f, size_t total,
+                          double* __restrict__ part) {
+  constexpr int NDOT = AA_MAX * (AA_MAX + 1) / 2 + AA_MAX;
+  double re[NDOT], im[NDOT];
+#pragma unroll
+  for (int q = 0; q < NDOT; ++q) re[q] = im[q] = 0.0;
+  const int m = v.m;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    double2 a[AA_MAX];
+#pragma unroll
+    for (int i = 0; i < AA_MAX; ++i) a[i] = i < m ? v.dF[i][e] : make_double2(0.0, 0.0);
+    const double2 fe = f[e];
+    int q = 0;
+#pragma unroll
+    for (int i = 0; i < AA_MAX; ++i) {
+#pragma unroll
+      for (int j = i; j < AA_MAX; ++j, ++q) {      // conj(a_i) a_j
+        re[q] += a[i].x * a[j].x + a[i].y * a[j].y;
+        im[q] += a[i].x * a[j].y - a[i].y * a[j].x;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < AA_MAX; ++i, ++q) {        // conj(a_i) f
+      re[q] += a[i].x * fe.x + a[i].y * fe.y;
+      im[q] += a[i].x * fe.y - a[i].y * fe.x;
+    }
+  }
+  __shared__ double red[256];
+  for (int q = 0; q < NDOT; ++q) {
+    for (int c = 0; c < 2; ++c) {
+      red[threadIdx.x] = c ? im[q] : re[q];
+      __syncthreads();
+      for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) part[((size_t)blockIdx.x * NDOT + q) * 2 + c] = red[0];
+      __syncthreads();
+    }
+  }
+}
+
+struct AaCoef {
+  double2 g[AA_MAX];
+  double lambda;
+};
+
+// Sm <- Sm + lambda f - sum_i g_i (dX_i + lambda dF_i)
+__global__ void k_aa_update(const __grid_constant__ AaVecs v, const __grid_constant__ AaCoef cf,
+                            const double2* __restrict__ f, double2* __restrict__ Sm, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    double2 x = Sm[e];
+    x.x += cf.lambda * f[e].x;
+    x.y += cf.lambda * f[e].y;
+    for (int i = 0; i < v.m; ++i) {
+      const double2 d = make_double2(v.dX[i][e].x + cf.lambda * v.dF[i][e].x, v.dX[i][e].y + cf.lambda * v.dF[i][e].y);
+      const double2 t = cmul(cf.g[i], d);
+      x.x -= t.x;
+      x.y -= t.y;
+    }
+    Sm[e] = x;
   }
 }
 
@@ -562,14 +656,81 @@ struct SeState {
   double* part = nullptr;
   int* err = nullptr;
   bool ready = false;                // g0 holds the atomic Lambda of the current build, Sm the mixed Sigma~
+  int aa_depth = 0;                  // 0: linear mixing; 1..AA_MAX: Anderson depth
+  int aa_count = 0;                  // iterates seen since the last reset
+  double2* aa_f = nullptr;           // current residual
+  double2* aa_fprev = nullptr;
+  double2* aa_xprev = nullptr;
+  double2* aa_dF[AA_MAX] = {};
+  double2* aa_dX[AA_MAX] = {};
+  double* aa_part = nullptr;         // per-block partial inner products
   int steps = 0;
 };
+
+void free_aa(SeState* st) {
+  void* ptrs[] = {st->aa_f, st->aa_fprev, st->aa_xprev, st->aa_part};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  st->aa_f = st->aa_fprev = st->aa_xprev = nullptr;
+  st->aa_part = nullptr;
+  for (int i = 0; i < AA_MAX; ++i) {
+    if (st->aa_dF[i]) cudaFree(st->aa_dF[i]);
+    if (st->aa_dX[i]) cudaFree(st->aa_dX[i]);
+    st->aa_dF[i] = st->aa_dX[i] = nullptr;
+  }
+}
 
 void free_state(SeState* st) {
   void* ptrs[] = {st->g0, st->Sm, st->FT, st->conn, st->w1, st->w2, st->St, st->tr, st->Q, st->paths, st->part,
                   st->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  free_aa(st);
+}
+
+// complex Gaussian elimination with partial pivoting of the m x m system (row-major), in place;
+// false when a pivot vanishes
+bool small_solve(std::vector<double2>& A, std::vector<double2>& b, int m) {
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    double best = -1.0;
+    for (int r = k; r < m; ++r) {
+      const double v = A[r * m + k].x * A[r * m + k].x + A[r * m + k].y * A[r * m + k].y;
+      if (v > best) {
+        best = v;
+        p = r;
+      }
+    }
+    if (!(best > 0.0)) return false;
+    if (p != k) {
+      for (int c = 0; c < m; ++c) std::swap(A[k * m + c], A[p * m + c]);
+      std::swap(b[k], b[p]);
+    }
+    const double2 pv = A[k * m + k];
+    const double2 inv = make_double2(pv.x / best, -pv.y / best);
+    for (int r = k + 1; r < m; ++r) {
+      const double2 a = A[r * m + k];
+      const double2 f = make_double2(a.x * inv.x - a.y * inv.y, a.x * inv.y + a.y * inv.x);
+      for (int c = k; c < m; ++c) {
+        const double2 t = A[k * m + c];
+        A[r * m + c].x -= f.x * t.x - f.y * t.y;
+        A[r * m + c].y -= f.x * t.y + f.y * t.x;
+      }
+      b[r].x -= f.x * b[k].x - f.y * b[k].y;
+      b[r].y -= f.x * b[k].y + f.y * b[k].x;
+    }
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    double2 acc = b[k];
+    for (int c = k + 1; c < m; ++c) {
+      acc.x -= A[k * m + c].x * b[c].x - A[k * m + c].y * b[c].y;
+      acc.y -= A[k * m + c].x * b[c].y + A[k * m + c].y * b[c].x;
+    }
+    const double2 pv = A[k * m + k];
+    const double d = pv.x * pv.x + pv.y * pv.y;
+    b[k] = make_double2((acc.x * pv.x + acc.y * pv.y) / d, (acc.y * pv.x - acc.x * pv.y) / d);
+  }
+  return true;
 }
 
 dim3 tiles32(int n, int Nr) { return dim3((n + 31) / 32, (n + 31) / 32, Nr); }
@@ -638,6 +799,78 @@ int prepare(dyson_ctx* c) {
   DY_CUDA(c, cudaMemsetAsync(st->Sm, 0, blk, c->stream));
   st->ready = true;
   st->steps = 0;
+  st->aa_count = 0;
+  return DYSON_OK;
+}
+
+// Anderson update of st->Sm from the new Sigma~ in st->St (buffers allocated on first use)
+int anderson_update(dyson_ctx* c, SeState* st, double mix) {
+  const size_t n_el = (size_t)c->Nr * c->Nc * c->Nc, blk = n_el * sizeof(double2);
+  const int m = st->aa_depth;
+  constexpr int NDOT = AA_MAX * (AA_MAX + 1) / 2 + AA_MAX;
+  if (!st->aa_f) {
+    bool ok = cudaMalloc(&st->aa_f, blk) == cudaSuccess && cudaMalloc(&st->aa_fprev, blk) == cudaSuccess &&
+              cudaMalloc(&st->aa_xprev, blk) == cudaSuccess &&
+              cudaMalloc(&st->aa_part, (size_t)MIX_BLOCKS * NDOT * 2 * sizeof(double)) == cudaSuccess;
+    for (int i = 0; i < AA_MAX && ok; ++i)
+      ok = cudaMalloc(&st->aa_dF[i], blk) == cudaSuccess && cudaMalloc(&st->aa_dX[i], blk) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      free_aa(st);
+      return ctx_fail(c, DYSON_ERR_OOM, "Anderson history buffers");
+    }
+  }
+  const int slot = (st->aa_count - 1 + AA_MAX) % AA_MAX;   // where the newest difference pair goes
+  const unsigned eblocks = (unsigned)std::min<size_t>((n_el + 255) / 256, 8192);
+  k_aa_push<<<eblocks, 256, 0, c->stream>>>(st->St, st->Sm, st->aa_f, st->aa_fprev, st->aa_xprev,
+                                            st->aa_dF[slot], st->aa_dX[slot], st->aa_count > 0 ? 1 : 0, n_el);
+  c->launches += 1;
+  const int mk = std::min(st->aa_count, m);
+  st->aa_count += 1;
+  AaVecs v{};
+  v.m = mk;
+  for (int i = 0; i < mk; ++i) {                           // the mk newest pairs
+    const int sl = (slot - i + AA_MAX) % AA_MAX;
+    v.dF[i] = st->aa_dF[sl];
+    v.dX[i] = st->aa_dX[sl];
+  }
+  AaCoef cf{};
+  cf.lambda = mix;
+  if (mk > 0) {
+    k_aa_dots<<<MIX_BLOCKS, 256, 0, c->stream>>>(v, st->aa_f, n_el, st->aa_part);
+    c->launches += 1;
+    std::vector<double> part((size_t)MIX_BLOCKS * NDOT * 2);
+    DY_CUDA(c, cudaMemcpyAsync(part.data(), st->aa_part, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+    DY_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::vector<double2> dots(NDOT, make_double2(0.0, 0.0));
+    for (int bk = 0; bk < MIX_BLOCKS; ++bk)
+      for (int q = 0; q < NDOT; ++q) {
+        dots[q].x += part[((size_t)bk * NDOT + q) * 2];
+        dots[q].y += part[((size_t)bk * NDOT + q) * 2 + 1];
+      }
+    // normal equations (dF^H dF + reg) gamma = dF^H f
+    std::vector<double2> A((size_t)mk * mk), rhs(mk);
+    double trace = 0.0;
+    int q = 0;
+    for (int i = 0; i < AA_MAX; ++i)
+      for (int j = i; j < AA_MAX; ++j, ++q) {
+        if (i >= mk || j >= mk) continue;
+        A[i * mk + j] = dots[q];
+        A[j * mk + i] = make_double2(dots[q].x, -dots[q].y);
+        if (i == j) trace += dots[q].x;
+      }
+    for (int i = 0; i < AA_MAX; ++i, ++q)
+      if (i < mk) rhs[i] = dots[q];
+    for (int i = 0; i < mk; ++i) A[i * mk + i].x += 1e-12 * trace;
+    if (small_solve(A, rhs, mk))
+      for (int i = 0; i < mk; ++i) cf.g[i] = rhs[i];
+    else
+      v.m = 0;                                             // degenerate history: plain mixing this step
+  }
+  k_aa_update<<<eblocks, 256, 0, c->stream>>>(v, cf, st->aa_f, st->Sm, n_el);
+  c->launches += 1;
+  DY_CUDA(c, cudaGetLastError());
   return DYSON_OK;
 }
 
@@ -658,6 +891,18 @@ void se_release(dyson_ctx* c) {
 void launch_export_diagonal(const double2* G, const int* src_site, int Nc, int ncol, int nq, double2* out,
                             cudaStream_t s) {
   k_export_diagonal<<<dim3((Nc + 31) / 32, (Nc + 31) / 32, nq), dim3(32, 8), 0, s>>>(G, src_site, Nc, ncol, out);
+}
+
+extern "C" int dyson_selfenergy_set_anderson(dyson_ctx* c, int32_t depth) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (depth < 0 || depth > AA_MAX)
+    return ctx_fail(c, DYSON_ERR_INVALID_ARG, "Anderson depth must be 0.." + std::to_string(AA_MAX));
+  DeviceGuard g(c->device);
+  int rc;
+  if ((rc = ensure_state(c))) return rc;
+  state(c)->aa_depth = depth;
+  state(c)->aa_count = 0;
+  return DYSON_OK;
 }
 
 extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mix, double* sigma_tilde,
@@ -701,12 +946,13 @@ extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mi
   DY_CUDA(c, cudaGetLastError());
   if (sigma_tilde)
     DY_CUDA(c, cudaMemcpyAsync(sigma_tilde, st->St, n_el * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-  // measure and mixing on Sigma~
-  k_se_mix<<<MIX_BLOCKS, 256, 0, c->stream>>>(st->St, st->Sm, n_el, mix, st->part);
+  // measure and mixing on Sigma~ (linear, Eq. (Sigmamix), or Anderson)
+  k_se_mix<<<MIX_BLOCKS, 256, 0, c->stream>>>(st->St, st->Sm, n_el, mix, st->part, st->aa_depth == 0 ? 1 : 0);
   c->launches += 1;
   DY_CUDA(c, cudaGetLastError());
   std::vector<double> part(2 * MIX_BLOCKS);
   DY_CUDA(c, cudaMemcpyAsync(part.data(), st->part, part.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (st->aa_depth > 0 && (rc = anderson_update(c, st, mix))) return rc;
   // B = G0 (G0 - Sigma~ + u v^T / 2)^-1 G0 replaces Lambda
   k_se_complete<<<eblocks, 256, 0, c->stream>>>(st->g0, st->Sm, Nc, c->Nt, n_el, st->w1);
   c->launches += 1;

@@ -13,12 +13,15 @@ from . import binding
 
 
 def self_consistent(solver, mix=0.7, delta_sc=None, max_iter=40, precision=binding.PREC_F64, tol=1e-13,
-                    max_sweeps=400):
+                    max_sweeps=400, anderson=0):
     """Run the loop on a Solver whose Lambda has been built.  Returns a dict with the
     iteration count, the history of the measure, whether it converged, the last
-    local Green's functions (device tensor [Nr, Nc, Nc]) and the solve reports."""
+    local Green's functions (device tensor [Nr, Nc, Nc]) and the solve reports.
+    anderson: 0 mixes linearly (Eq. (Sigmamix)); 1..6 accelerates with Anderson mixing
+    of that depth (dyson_selfenergy_set_anderson)."""
     if delta_sc is None:
         delta_sc = 1e-8
+    solver.set_anderson(anderson)
     gloc = None
     hist, reports = [], []
     converged = False
