@@ -205,6 +205,13 @@ def selfenergy_leg(args, dev, stream):
     secs = time.perf_counter() - t0
     n_conn, ms_conn = s.profile_query(7)
     s.profile(False)
+    # the same loop with Anderson acceleration (depth 5) in place of the linear mixing
+    s.build_sigma()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    ra = self_consistent(s, mix=0.7, max_iter=40, precision=binding.PREC_TF32X3_F64REF, tol=1e-10, anderson=5)
+    torch.cuda.synchronize(dev)
+    secs_aa = time.perf_counter() - t0
     s.close()
     its = r["iterations"]
     flops = 8.0 * p.Nc ** 4 * p.Nr                   # the [Nc]^4 contraction per site, complex MACs x 8
@@ -215,6 +222,8 @@ def selfenergy_leg(args, dev, stream):
             "delta_sc": r["delta_sc"], "history": [float(f"{h:.3e}") for h in r["history"]],
             "seconds": secs, "seconds_per_iteration": secs / its,
             "lattice_solve_sweeps_per_iteration": [q["sweeps"] for q in r["reports"]],
+            "anderson5": {"iterations": ra["iterations"], "converged": ra["converged"], "seconds": secs_aa,
+                          "history": [float(f"{h:.3e}") for h in ra["history"]]},
             "selfenergy_conn": {"launches": n_conn, "avg_ms": ms_conn / n_conn if n_conn else None,
                                 "share_of_loop": ms_conn * 1e-3 / secs,
                                 "roofline": {"bound": "alu", "achieved": ach, "peak": NOMINAL_FP64_TFLOPS,
