@@ -2,9 +2,11 @@
 
 Block columns (source sites) are independent right-hand sides of the Dyson
 equation (Sec. IV.D: every unit vector is solved on its own), so ranks share
-nothing while they sweep.  The only collectives are host-side bookkeeping:
+nothing while they sweep.  The lattice solve needs only host-side bookkeeping:
 a barrier and a max-reduction around timed regions, and one final all-gather
-that merges per-site observables.  None sits on the data path.
+that merges per-site observables.  The self-consistency loop of Sec. IV.C has
+one real exchange per iteration: every site's self-energy needs the local Green's
+functions of its neighbours, which other ranks solved (sum_rows_).
 """
 from __future__ import annotations
 
@@ -89,3 +91,15 @@ def all_gather_observables(local: np.ndarray, device=None) -> np.ndarray:
     bufs = [torch.empty_like(t) for _ in range(dist.get_world_size())]
     dist.all_gather(bufs, t)
     return merge_observables([b.cpu().numpy() for b in bufs])
+
+
+def sum_rows_(t):
+    """In place, sum a tensor over the ranks (each rank holds its own rows, zeros elsewhere,
+    so the sum is the merge); a complex tensor travels as its real view.  Identity when not
+    distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return t
+    dist.all_reduce(torch.view_as_real(t) if t.is_complex() else t, op=dist.ReduceOp.SUM)
+    return t

@@ -145,3 +145,12 @@ def test_anderson_depth_is_checked(torch_cuda, lib):
     with pytest.raises(binding.DysonError, match="INVALID_ARG"):
         s.set_anderson(7)
     s.set_anderson(0)
+
+
+def test_sharded_loop_in_one_process_is_the_plain_loop(torch_cuda, lib):
+    from paper_1309_5994_gb300.selfconsistency import self_consistent, self_consistent_sharded
+    p = wl.small(**SMALL)
+    a = self_consistent(_solver(p), mix=0.7, delta_sc=1e-10, max_iter=60, precision=0, tol=1e-14)
+    b = self_consistent_sharded(_solver(p), mix=0.7, delta_sc=1e-10, max_iter=60, precision=0, tol=1e-14)
+    assert a["iterations"] == b["iterations"] and np.allclose(a["history"], b["history"], rtol=1e-9, atol=0)
+    assert torch_cuda.equal(a["gloc"], b["gloc"])
