@@ -299,9 +299,8 @@ __global__ void __launch_bounds__(CONN_THREADS) k_se_conn(const uint32_t* __rest
   if (live) conn[((size_t)i * Nc + a) * Nc + d] = acc;
 }
 
-// batched complex GEMM C_i = op(A_i) B_i (op: 0 = none, 1 = conjugate transpose), 32 x 32 tiles
-__global__ void k_zgemm(const double2* __restrict__ A, const double2* __restrict__ B, double2* __restrict__ C, int n,
-                        int opA) {
+// batched complex GEMM C_i = A_i B_i, 32 x 32 tiles
+__global__ void k_zgemm(const double2* __restrict__ A, const double2* __restrict__ B, double2* __restrict__ C, int n) {
   __shared__ double2 As[32][33], Bs[32][33];
   const int i = blockIdx.z;
   const int row0 = blockIdx.y * 32, col0 = blockIdx.x * 32;
@@ -314,14 +313,8 @@ __global__ void k_zgemm(const double2* __restrict__ A, const double2* __restrict
     for (int r = 0; r < 4; ++r) {
       const int rr = ty + 8 * r;
       double2 av = make_double2(0.0, 0.0), bv = make_double2(0.0, 0.0);
-      if (opA == 0) {
-        if (row0 + rr < n && k0 + tx < n) av = Ai[(size_t)(row0 + rr) * n + k0 + tx];
-        As[rr][tx] = av;                                  // As[row][k]
-      } else {
-        // op(A)(row, k) = conj(A(k, row)): read A rows k0.. coalesced along row
-        if (k0 + rr < n && row0 + tx < n) av = Ai[(size_t)(k0 + rr) * n + row0 + tx];
-        As[tx][rr] = make_double2(av.x, -av.y);
-      }
+      if (row0 + rr < n && k0 + tx < n) av = Ai[(size_t)(row0 + rr) * n + k0 + tx];
+      As[rr][tx] = av;                                    // As[row][k]
       if (k0 + rr < n && col0 + tx < n) bv = Bi[(size_t)(k0 + rr) * n + col0 + tx];
       Bs[rr][tx] = bv;                                    // Bs[k][col]
     }
@@ -388,8 +381,8 @@ __global__ void k_se_complete(const double2* __restrict__ g0, const double2* __r
   }
 }
 
-// out_i = A_i^T, conjugated when conj != 0
-__global__ void k_transpose(const double2* __restrict__ A, int n, int conj, double2* __restrict__ out) {
+// out_i = A_i^T
+__global__ void k_transpose(const double2* __restrict__ A, int n, double2* __restrict__ out) {
   __shared__ double2 tile[32][33];
   const int i = blockIdx.z;
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
@@ -401,8 +394,7 @@ __global__ void k_transpose(const double2* __restrict__ A, int n, int conj, doub
   for (int r = threadIdx.y; r < 32; r += 8) {
     const int row = c0 + r, col = r0 + threadIdx.x;
     if (row < n && col < n) {
-      const double2 v = tile[threadIdx.x][r];
-      out[((size_t)i * n + row) * n + col] = make_double2(v.x, conj ? -v.y : v.y);
+      out[((size_t)i * n + row) * n + col] = tile[threadIdx.x][r];
     }
   }
 }
@@ -664,7 +656,6 @@ struct SeState {
   double2* aa_dF[AA_MAX] = {};
   double2* aa_dX[AA_MAX] = {};
   double* aa_part = nullptr;         // per-block partial inner products
-  int steps = 0;
 };
 
 void free_aa(SeState* st) {
@@ -735,8 +726,8 @@ bool small_solve(std::vector<double2>& A, std::vector<double2>& b, int m) {
 
 dim3 tiles32(int n, int Nr) { return dim3((n + 31) / 32, (n + 31) / 32, Nr); }
 
-int gemm(dyson_ctx* c, const double2* A, const double2* B, double2* C, int opA) {
-  k_zgemm<<<tiles32(c->Nc, c->Nr), dim3(32, 8), 0, c->stream>>>(A, B, C, c->Nc, opA);
+int gemm(dyson_ctx* c, const double2* A, const double2* B, double2* C) {
+  k_zgemm<<<tiles32(c->Nc, c->Nr), dim3(32, 8), 0, c->stream>>>(A, B, C, c->Nc);
   c->launches += 1;
   DY_CUDA(c, cudaGetLastError());
   return DYSON_OK;
@@ -798,7 +789,6 @@ int prepare(dyson_ctx* c) {
   DY_CUDA(c, cudaMemcpyAsync(st->g0, c->d_lam, blk, cudaMemcpyDeviceToDevice, c->stream));
   DY_CUDA(c, cudaMemsetAsync(st->Sm, 0, blk, c->stream));
   st->ready = true;
-  st->steps = 0;
   st->aa_count = 0;
   return DYSON_OK;
 }
@@ -937,9 +927,9 @@ extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mi
   c->launches += 4;
   DY_CUDA(c, cudaGetLastError());
   // D1 = G0 F G0 (F = FT^T), Sigma~ = -conn - D1 + 2 tr(G0 F) G0
-  k_transpose<<<tiles32(Nc, Nr), dim3(32, 8), 0, c->stream>>>(st->FT, Nc, 0, st->w2);
+  k_transpose<<<tiles32(Nc, Nr), dim3(32, 8), 0, c->stream>>>(st->FT, Nc, st->w2);
   c->launches += 1;
-  if ((rc = gemm(c, st->g0, st->w2, st->w1, 0)) || (rc = gemm(c, st->w1, st->g0, st->w2, 0))) return rc;
+  if ((rc = gemm(c, st->g0, st->w2, st->w1)) || (rc = gemm(c, st->w1, st->g0, st->w2))) return rc;
   const unsigned eblocks = (unsigned)std::min<size_t>((n_el + 255) / 256, 8192);
   k_se_combine<<<eblocks, 256, 0, c->stream>>>(st->conn, st->w2, st->tr, st->g0, (size_t)Nc * Nc, n_el, st->St);
   c->launches += 1;
@@ -958,13 +948,12 @@ extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mi
   c->launches += 1;
   DY_CUDA(c, cudaMemcpyAsync(st->conn, st->g0, n_el * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   if ((rc = solve(c, st, st->w1, st->conn, "local Dyson equation"))) return rc;
-  if ((rc = gemm(c, st->g0, st->conn, st->w2, 0))) return rc;
+  if ((rc = gemm(c, st->g0, st->conn, st->w2))) return rc;
   DY_CUDA(c, cudaMemcpyAsync(c->d_lam, st->w2, n_el * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
   c->lam32_built = c->lam_split_built = false;
   oz_invalidate(c);
   c->se_installed = true;
-  st->steps += 1;
   double ss = 0.0, mx = 0.0;
   for (int b = 0; b < MIX_BLOCKS; ++b) {
     ss += part[2 * b];
