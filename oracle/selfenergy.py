@@ -53,9 +53,11 @@ Readings (the paper does not fix them):
 Parity: the two-particle machinery is pinned by the atomic two-point function
 (its closed form, atomic.atomic_gf), Wick's theorem at U = 0 (the cumulant
 vanishes at every point, coincident ones included), the exchange antisymmetry of
-G2 and the equal-point value rho_d; B_i by the local Dyson equation.  The
-contraction and the self-consistency loop are the definitions written out:
-parity unpinned beyond those checks.
+G2 and the equal-point value rho_d; B_i by the local Dyson equation; and the
+whole step (cumulant, contraction, local block, loop) by physics: on the Hubbard
+dimer the O(J^2) term of the self-consistent local Green's function, extrapolated
+to dtau -> 0, is that of exact diagonalisation, which the lattice Dyson equation
+without self-energy misses (tests/test_oracle_selfenergy.py).
 """
 from __future__ import annotations
 
