@@ -56,8 +56,9 @@ vanishes at every point, coincident ones included), the exchange antisymmetry of
 G2 and the equal-point value rho_d; B_i by the local Dyson equation; and the
 whole step (cumulant, contraction, local block, loop) by physics: on the Hubbard
 dimer the O(J^2) term of the self-consistent local Green's function, extrapolated
-to dtau -> 0, is that of exact diagonalisation, which the lattice Dyson equation
-without self-energy misses (tests/test_oracle_selfenergy.py).
+to dtau, dt -> 0, is that of exact diagonalisation on the imaginary branch and on
+the real-time branch (G^>(t, 0)), which the lattice Dyson equation without
+self-energy misses (tests/test_oracle_selfenergy.py).
 """
 from __future__ import annotations
 
