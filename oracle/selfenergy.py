@@ -58,7 +58,10 @@ whole step (cumulant, contraction, local block, loop) by physics: on the Hubbard
 dimer the O(J^2) term of the self-consistent local Green's function, extrapolated
 to dtau, dt -> 0, is that of exact diagonalisation on the imaginary branch and on
 the real-time branch (G^>(t, 0)), which the lattice Dyson equation without
-self-energy misses (tests/test_oracle_selfenergy.py).
+self-energy misses; and the self-consistent fixed point restricted to the times
+of a shorter contour is that of the shorter contour to rounding, the discrete
+causality that a wrong branch order or weight would break
+(tests/test_oracle_selfenergy.py).
 """
 from __future__ import annotations
 

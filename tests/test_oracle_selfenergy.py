@@ -252,3 +252,22 @@ def test_real_time_second_order_term_is_that_of_exact_diagonalisation():
     scale = np.abs(exact[k]).max()
     assert np.abs(sc[k] - exact[k]).max() < 0.02 * scale
     assert np.abs(hi[k] - exact[k]).max() > 1.0 * scale
+
+
+def test_fixed_point_does_not_depend_on_where_the_real_branches_end():
+    """Entries of the self-consistent Sigma~ and G_loc whose times are all before the end of a
+    shorter contour are the same on a longer one (driven dimer): contributions later than every
+    external time cancel between the two real branches in the cumulant contraction as in the
+    lattice solve.  A wrong operator order or weight on one branch breaks the cancellation."""
+    U, J, beta, dt, Nm = 4.0, 0.3, 1.0, 0.1, 4
+
+    def prob(Nt):
+        return wl.uniform_problem("d", 2, Nt, Nm, dt, beta, 0.1, 0.0, U, J, Ly=1, aU=0.2, aJ=0.3, omega=3.0)
+
+    Ns, Nl = 4, 7
+    _, St_s, Gl_s, _, _ = se.self_consistent(prob(Ns), mix=0.7, delta_sc=1e-14, max_iter=80)
+    _, St_l, Gl_l, _, _ = se.self_consistent(prob(Nl), mix=0.7, delta_sc=1e-14, max_iter=80)
+    ix = np.array(list(range(Ns)) + [2 * Nl - Ns + j for j in range(Ns)] + [2 * Nl + m for m in range(Nm)])
+    assert np.abs(St_s).max() > 1e-3
+    assert np.abs(St_l[:, ix][:, :, ix] - St_s).max() < 1e-14
+    assert np.abs(Gl_l[:, ix][:, :, ix] - Gl_s).max() < 1e-13
