@@ -694,6 +694,8 @@ int dyson_local_greens(dyson_ctx* c, const int32_t* src, int64_t n_src, int prec
                        int32_t max_sweeps, double* gloc, dyson_report* rep_out) {
   if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
   if (!gloc) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "gloc is NULL");
+  if (c->symmetry == DYSON_SYMMETRY_C4V)
+    return local_greens_c4v(c, src, n_src, precision, tol, max_sweeps, gloc, rep_out);
   return solve_columns_impl(c, src, n_src, precision, tol, max_sweeps, nullptr, gloc, rep_out);
 }
 

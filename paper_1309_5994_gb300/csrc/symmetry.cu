@@ -108,22 +108,47 @@ extern "C" int dyson_set_symmetry(dyson_ctx* c, int mode) {
   return DYSON_OK;
 }
 
-int solve_columns_c4v(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
-                      int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
+namespace {
+
+// one representative per requested orbit, in order of first appearance; slot[r] = its position
+int orbit_representatives(dyson_ctx* c, const int32_t* src, int64_t n_src, std::vector<int32_t>* reps,
+                          std::vector<int>* slot) {
   if (n_src < 1 || !src) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "need at least one source site");
   for (int64_t q = 0; q < n_src; ++q)
     if (src[q] < 0 || src[q] >= c->Nr) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "source site out of range");
-  DeviceGuard dg(c->device);
-  // one representative per requested orbit, in order of first appearance
-  std::vector<int32_t> reps;
-  std::vector<int> slot(c->Nr, -1);
+  slot->assign(c->Nr, -1);
+  reps->clear();
   for (int64_t q = 0; q < n_src; ++q) {
     const int r = c->sym_rep[src[q]];
-    if (slot[r] < 0) {
-      slot[r] = (int)reps.size();
-      reps.push_back(r);
+    if ((*slot)[r] < 0) {
+      (*slot)[r] = (int)reps->size();
+      reps->push_back(r);
     }
   }
+  return DYSON_OK;
+}
+
+// observables of each requested site s are those of its representative
+void copy_observables(dyson_ctx* c, const int32_t* src, int64_t n_src) {
+  const size_t NrNt = (size_t)c->Nr * c->Nt;
+  for (int64_t q = 0; q < n_src; ++q) {
+    const int s = src[q], r = c->sym_rep[s];
+    if (s != r)
+      for (int k = 0; k < 3; ++k)
+        cudaMemcpyAsync(c->d_obs + k * NrNt + (size_t)s * c->Nt, c->d_obs + k * NrNt + (size_t)r * c->Nt,
+                        c->Nt * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  }
+}
+
+}  // namespace
+
+int solve_columns_c4v(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
+                      int32_t max_sweeps, double* g_out, dyson_report* rep_out) {
+  std::vector<int32_t> reps;
+  std::vector<int> slot;
+  int rc0 = orbit_representatives(c, src, n_src, &reps, &slot);
+  if (rc0) return rc0;
+  DeviceGuard dg(c->device);
   const size_t blk = (size_t)c->Nc * c->Nc;                  // one site's Nc x Nc block
   const size_t col = (size_t)c->Nr * blk;                    // one block column
   double2* tmp = nullptr;
@@ -139,13 +164,9 @@ int solve_columns_c4v(dyson_ctx* c, const int32_t* src, int64_t n_src, int preci
                                reinterpret_cast<double*>(tmp), rep_out);
   c->symmetry = DYSON_SYMMETRY_C4V;
   if (rc == DYSON_OK || rc == DYSON_ERR_NOT_CONVERGED || rc == DYSON_ERR_DIVERGED) {
-    const size_t NrNt = (size_t)c->Nr * c->Nt;
+    copy_observables(c, src, n_src);
     for (int64_t q = 0; q < n_src; ++q) {
       const int s = src[q], r = c->sym_rep[s];
-      if (s != r)                                            // observables of s are those of r
-        for (int k = 0; k < 3; ++k)
-          cudaMemcpyAsync(c->d_obs + k * NrNt + (size_t)s * c->Nt, c->d_obs + k * NrNt + (size_t)r * c->Nt,
-                          c->Nt * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
       if (g_out) {                                           // G_{j,s} = G_{g^-1(j), r}
         const int g = c->sym_op[s];
         k_permute_sites<<<dim3((unsigned)std::min<size_t>((blk + 255) / 256, 64), c->Nr), 256, 0, c->stream>>>(
@@ -158,5 +179,31 @@ int solve_columns_c4v(dyson_ctx* c, const int32_t* src, int64_t n_src, int preci
     if (e != cudaSuccess) rc = ctx_fail(c, DYSON_ERR_CUDA, std::string("C4v fill: ") + cudaGetErrorString(e));
   }
   if (tmp) cudaFree(tmp);
+  return rc;
+}
+
+int local_greens_c4v(dyson_ctx* c, const int32_t* src, int64_t n_src, int precision, double tol,
+                     int32_t max_sweeps, double* gloc, dyson_report* rep_out) {
+  std::vector<int32_t> reps;
+  std::vector<int> slot;
+  int rc = orbit_representatives(c, src, n_src, &reps, &slot);
+  if (rc) return rc;
+  DeviceGuard dg(c->device);
+  c->symmetry = DYSON_SYMMETRY_NONE;
+  rc = dyson_local_greens(c, reps.data(), (int64_t)reps.size(), precision, tol, max_sweeps, gloc, rep_out);
+  c->symmetry = DYSON_SYMMETRY_C4V;
+  if (rc == DYSON_OK || rc == DYSON_ERR_NOT_CONVERGED || rc == DYSON_ERR_DIVERGED) {
+    copy_observables(c, src, n_src);
+    const size_t blk = (size_t)c->Nc * c->Nc;
+    double2* G = reinterpret_cast<double2*>(gloc);
+    for (int64_t q = 0; q < n_src; ++q) {
+      const int s = src[q], r = c->sym_rep[s];
+      if (s != r)
+        cudaMemcpyAsync(G + (size_t)s * blk, G + (size_t)r * blk, blk * sizeof(double2), cudaMemcpyDeviceToDevice,
+                        c->stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = ctx_fail(c, DYSON_ERR_CUDA, std::string("C4v fill: ") + cudaGetErrorString(e));
+  }
   return rc;
 }

@@ -154,3 +154,50 @@ def test_sharded_loop_in_one_process_is_the_plain_loop(torch_cuda, lib):
     b = self_consistent_sharded(_solver(p), mix=0.7, delta_sc=1e-10, max_iter=60, precision=0, tol=1e-14)
     assert a["iterations"] == b["iterations"] and np.allclose(a["history"], b["history"], rtol=1e-9, atol=0)
     assert torch_cuda.equal(a["gloc"], b["gloc"])
+
+
+def test_c4v_loop_solves_one_site_per_orbit(torch_cuda, lib):
+    """App. A inside the loop of Sec. IV.C: with a centred trap and a uniform drive the local
+    Green's functions of one site per orbit (the others are copies, G_{g(r),g(r)} = G_{r,r})
+    give the fixed point of the loop that solves every site, from 3 block columns per iteration
+    instead of 9 on the 3x3 lattice (corners, edges, centre)."""
+    from paper_1309_5994_gb300 import binding
+    from paper_1309_5994_gb300.selfconsistency import self_consistent
+    p = wl.small(L=3, Ly=3, Nt=6, Nm=4, dt=0.1, beta=1.0, U0=10.0, J0=1.0, trap_c=0.3, aU=0.1, aJ=0.2,
+                 omega=6.0)
+    out = {}
+    for mode in (binding.SYMMETRY_NONE, binding.SYMMETRY_C4V):
+        s = _solver(p)
+        s.set_symmetry(mode)
+        out[mode] = self_consistent(s, mix=0.7, delta_sc=1e-11, max_iter=60, precision=0, tol=1e-14)
+        out[mode]["lam"] = s.sigma()
+        s.close()
+    a, b = out[binding.SYMMETRY_NONE], out[binding.SYMMETRY_C4V]
+    assert a["converged"] and b["converged"] and abs(a["iterations"] - b["iterations"]) <= 1
+    ga, gb = a["gloc"].cpu().numpy(), b["gloc"].cpu().numpy()
+    assert np.abs(gb - ga).max() <= 1e-10 * np.abs(ga).max()
+    assert np.abs(b["lam"] - a["lam"]).max() <= 1e-10 * np.abs(a["lam"]).max()
+    fa = sum(r["gemm_flops"] for r in a["reports"]) / a["iterations"]
+    fb = sum(r["gemm_flops"] for r in b["reports"]) / b["iterations"]
+    assert fb < 0.45 * fa
+
+
+def test_fixed_point_does_not_depend_on_where_the_real_branches_end(torch_cuda, lib):
+    """Causality of the whole loop on the GPU: the self-consistent local Green's functions of a
+    driven lattice with Nt = 4, restricted to their times, are those of the same lattice with
+    Nt = 7 (contributions later than every external time cancel between the real branches in
+    the lattice solve and in the cumulant contraction)."""
+    from paper_1309_5994_gb300.selfconsistency import self_consistent
+    kw = dict(SMALL)
+    Nm = kw["Nm"]
+    g = {}
+    for Nt in (4, 7):
+        kw["Nt"] = Nt
+        s = _solver(wl.small(**kw))
+        r = self_consistent(s, mix=0.7, delta_sc=1e-12, max_iter=80, precision=0, tol=1e-14)
+        assert r["converged"]
+        g[Nt] = r["gloc"].cpu().numpy()
+        s.close()
+    Ns, Nl = 4, 7
+    ix = np.array(list(range(Ns)) + [2 * Nl - Ns + j for j in range(Ns)] + [2 * Nl + m for m in range(Nm)])
+    assert np.abs(g[Nl][:, ix][:, :, ix] - g[Ns]).max() <= 1e-11 * np.abs(g[Ns]).max()
