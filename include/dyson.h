@@ -227,6 +227,9 @@ int dyson_local_greens(dyson_ctx* ctx, const int32_t* src_sites, int64_t n_src, 
  *                (N_bd = Nr Nc^2 block-diagonal entries), Sec. IV.C's measure taken on Sigma~
  *                (Sigma itself divides by a singular value of G0 that falls exponentially
  *                with the real-time branch length).
+ * With DYSON_SYMMETRY_C4V set, the cumulant contraction runs for one site per
+ * orbit and the other sites take their representative's (App. A); gloc must
+ * then be C4v-invariant, as dyson_local_greens under C4v returns it.
  * dyson_build_sigma returns to Sigma = 0.  Device memory: 7 Nr Nc^2 complex128.
  * Returns INVALID_ARG for mix outside (0, 1] or a NULL gloc, STATE before
  * dyson_build_sigma or with Lambda transposed, DIVERGED if a local system is

@@ -167,9 +167,9 @@ __global__ void k_se_hyb(const double2* __restrict__ gloc, const double2* __rest
 // On the real branches |exp(+i Phi)| = 1, so differences of these sums lose nothing to
 // cancellation; the imaginary branch, whose factors span exp(+-beta E), is summed directly.
 __global__ void k_se_prefix(const double2* __restrict__ phase, const double2* __restrict__ FT, int Nt, int Nm,
-                            double2* __restrict__ Q) {
+                            const int* __restrict__ sites, double2* __restrict__ Q) {
   const int Nc = 2 * Nt + Nm, R = 2 * Nt;
-  const int i = blockIdx.y;
+  const int i = sites ? sites[blockIdx.y] : blockIdx.y;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * Nc) return;
   const int p = t / Nc, b = t % Nc;
@@ -185,7 +185,8 @@ __global__ void k_se_prefix(const double2* __restrict__ phase, const double2* __
 }
 
 // connected part: conn_i(a, d) = sum_{b,c} [G2_{up up} + G2_{up dn}](a, b; c, d) F_i(c, b)
-// grid (ceil(Nc^2 / 256), Nr), 256 threads, one (a, d) per thread.  Per b the creator point c
+// grid (ceil(Nc^2 / 256), sites), 256 threads, one (a, d) per thread; blockIdx.y indexes `sites`
+// (all sites in order when NULL).  Per b the creator point c
 // runs through four intervals of fixed operator order: their real-branch parts come from the
 // prefix sums Q, their imaginary-branch parts are summed directly.
 constexpr int CONN_THREADS = 256;
@@ -193,10 +194,11 @@ __global__ void __launch_bounds__(CONN_THREADS) k_se_conn(const uint32_t* __rest
                                                            const double2* __restrict__ phase,
                                                            const double2* __restrict__ FT,
                                                            const double2* __restrict__ Q, int Nt, int Nm,
+                                                           const int* __restrict__ sites,
                                                            double2* __restrict__ conn) {
   extern __shared__ double2 sm[];
   const int Nc = 2 * Nt + Nm, R = 2 * Nt;
-  const int i = blockIdx.y;
+  const int i = sites ? sites[blockIdx.y] : blockIdx.y;
   double2* em = sm;                  // [2][Nc] exp(-i Phi_p(z)): annihilator factors
   double2* ep = em + 2 * Nc;         // [2][Nc] exp(+i Phi_p(z)): creator factors
   double2* Qs = ep + 2 * Nc;         // [2][R + 1] prefix sums of the current b
@@ -647,6 +649,7 @@ struct SeState {
   uint32_t* paths = nullptr;
   double* part = nullptr;
   int* err = nullptr;
+  int* reps = nullptr;               // [Nr] orbit representatives, when the context has C4v set
   bool ready = false;                // g0 holds the atomic Lambda of the current build, Sm the mixed Sigma~
   int aa_depth = 0;                  // 0: linear mixing; 1..AA_MAX: Anderson depth
   int aa_count = 0;                  // iterates seen since the last reset
@@ -673,7 +676,7 @@ void free_aa(SeState* st) {
 
 void free_state(SeState* st) {
   void* ptrs[] = {st->g0, st->Sm, st->FT, st->conn, st->w1, st->w2, st->St, st->tr, st->Q, st->paths, st->part,
-                  st->err};
+                  st->err, st->reps};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free_aa(st);
@@ -768,7 +771,8 @@ int ensure_state(dyson_ctx* c) {
        cudaMalloc(&st->tr, (size_t)c->Nr * sizeof(double2)) == cudaSuccess &&
        cudaMalloc(&st->paths, 256 * PATHS * sizeof(uint32_t)) == cudaSuccess &&
        cudaMalloc(&st->part, 2 * MIX_BLOCKS * sizeof(double)) == cudaSuccess &&
-       cudaMalloc(&st->err, (size_t)c->Nr * sizeof(int)) == cudaSuccess;
+       cudaMalloc(&st->err, (size_t)c->Nr * sizeof(int)) == cudaSuccess &&
+       cudaMalloc(&st->reps, (size_t)c->Nr * sizeof(int)) == cudaSuccess;
   const std::vector<uint32_t> tab = path_table();
   ok = ok && cudaMemcpy(st->paths, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!ok) {                                             // nothing half-built stays behind
@@ -916,12 +920,31 @@ extern "C" int dyson_selfenergy_step(dyson_ctx* c, const double* gloc, double mi
                       256 * PATHS * sizeof(uint32_t);
   if (smem > 48 * 1024)
     DY_CUDA(c, cudaFuncSetAttribute(k_se_conn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // with C4v the contraction runs for one site per orbit; a site s = g(r) has F_s = F_r and
+  // K_s = K_r (its neighbours' G_loc and its levels are images of r's), so conn_s = conn_r
+  std::vector<int> reps;
+  if (c->symmetry == DYSON_SYMMETRY_C4V && (int)c->sym_rep.size() == Nr)
+    for (int i = 0; i < Nr; ++i)
+      if (c->sym_rep[i] == i) reps.push_back(i);
+  const int n_conn = reps.empty() ? Nr : (int)reps.size();
+  const int* d_sites = nullptr;
+  if (!reps.empty()) {
+    DY_CUDA(c, cudaMemcpyAsync(st->reps, reps.data(), reps.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    d_sites = st->reps;
+  }
   {
     KernelTimer t(c, DYSON_KERNEL_SELFENERGY);
-    k_se_prefix<<<dim3((unsigned)((2 * Nc + 127) / 128), Nr), 128, 0, c->stream>>>(c->d_phase, st->FT, c->Nt,
-                                                                                  c->Nm, st->Q);
-    k_se_conn<<<dim3((unsigned)((Nc * Nc + CONN_THREADS - 1) / CONN_THREADS), Nr), CONN_THREADS, smem,
-                c->stream>>>(st->paths, c->d_phase, st->FT, st->Q, c->Nt, c->Nm, st->conn);
+    k_se_prefix<<<dim3((unsigned)((2 * Nc + 127) / 128), n_conn), 128, 0, c->stream>>>(c->d_phase, st->FT, c->Nt,
+                                                                                      c->Nm, d_sites, st->Q);
+    k_se_conn<<<dim3((unsigned)((Nc * Nc + CONN_THREADS - 1) / CONN_THREADS), n_conn), CONN_THREADS, smem,
+                c->stream>>>(st->paths, c->d_phase, st->FT, st->Q, c->Nt, c->Nm, d_sites, st->conn);
+  }
+  if (!reps.empty()) {
+    const size_t blk = (size_t)Nc * Nc;
+    for (int i = 0; i < Nr; ++i)
+      if (c->sym_rep[i] != i)
+        DY_CUDA(c, cudaMemcpyAsync(st->conn + (size_t)i * blk, st->conn + (size_t)c->sym_rep[i] * blk,
+                                   blk * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
   }
   k_se_trace<<<Nr, 256, 0, c->stream>>>(st->g0, st->FT, Nc, st->tr);
   c->launches += 4;
