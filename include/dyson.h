@@ -320,8 +320,11 @@ int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
  * index of the orbit, about Nr/8 block columns for all sources.  It fills the
  * other sources' observables by copies, and their G, when g_out is given, by
  * the site permutation G_{j,s} = G_{g^-1(j),r} for s = g(r).  The report
- * counts the solved representatives only.  DYSON_SYMMETRY_NONE (the default)
- * solves every source. */
+ * counts the solved representatives only.  dyson_local_greens and
+ * dyson_selfenergy_step use the same reduction (see there).  The invariance is
+ * checked on the drive tables; local blocks installed by the self-energy step
+ * are taken to be invariant.  DYSON_SYMMETRY_NONE (the default) solves every
+ * source. */
 enum { DYSON_SYMMETRY_NONE = 0, DYSON_SYMMETRY_C4V = 1 };
 int dyson_set_symmetry(dyson_ctx* ctx, int mode);
 
