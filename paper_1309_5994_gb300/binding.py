@@ -179,6 +179,20 @@ class SolveResult:
     report: dict
 
 
+def device_buffer(t, dtype, numel: int, device, name: str):
+    """Raw pointer of the tensor `t` for a DEVICE argument of the C ABI, after checking
+    that it is a contiguous CUDA tensor of `dtype` with `numel` elements on GPU `device`
+    (None: any).  The library takes the pointer as it is, so a host or mis-sized tensor
+    is refused here, before any kernel could touch it."""
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} elements, not {t.numel()}")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{name} is on cuda:{t.device.index}; the context is on cuda:{device}")
+    return C.c_void_p(t.data_ptr())
+
+
 class Solver:
     """One context of the C ABI for a workloads.Problem-like object.
 
@@ -228,9 +242,8 @@ class Solver:
         rep = Report()
         gptr = None
         if g_out is not None:
-            assert g_out.is_cuda and g_out.dtype == self._torch.complex128 and g_out.is_contiguous()
-            assert g_out.numel() == len(src) * self.p.Nr * self.p.Nc * self.p.Nc
-            gptr = C.c_void_p(g_out.data_ptr())
+            gptr = device_buffer(g_out, self._torch.complex128, len(src) * self.p.Nr * self.p.Nc * self.p.Nc,
+                                 self.device, "g_out")
         rc = self.lib.dyson_solve_columns(self.h, src.ctypes.data_as(C.POINTER(C.c_int32)), len(src), precision,
                                           tol, max_sweeps, gptr, C.byref(rep))
         self._check(rc, ok=allow)
@@ -241,13 +254,13 @@ class Solver:
         tensor of shape [n, Nr, Nc].  Returns SolveResult."""
         s = np.ascontiguousarray(np.asarray(sites, dtype=np.int32))
         t = np.ascontiguousarray(np.asarray(times, dtype=np.int32))
-        assert s.shape == t.shape
+        if s.shape != t.shape:
+            raise ValueError("sites and times must have the same length")
         rep = Report()
         gptr = None
         if g_out is not None:
-            assert g_out.is_cuda and g_out.dtype == self._torch.complex128 and g_out.is_contiguous()
-            assert g_out.numel() == len(s) * self.p.Nr * self.p.Nc
-            gptr = C.c_void_p(g_out.data_ptr())
+            gptr = device_buffer(g_out, self._torch.complex128, len(s) * self.p.Nr * self.p.Nc, self.device,
+                                 "g_out")
         rc = self.lib.dyson_solve_vector_columns(self.h, s.ctypes.data_as(C.POINTER(C.c_int32)),
                                                  t.ctypes.data_as(C.POINTER(C.c_int32)), len(s), precision, tol,
                                                  max_sweeps, gptr, C.byref(rep))
@@ -258,7 +271,8 @@ class Solver:
         """(loss, dL/dU [Nr, Nt], dL/dJ [Nb, Nt], SolveResult) of L = sum_i w_i n_i(t_index)."""
         t_index = self.p.Nt - 1 if t_index is None else t_index
         w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
-        assert w.shape == (self.p.Nr,)
+        if w.shape != (self.p.Nr,):
+            raise ValueError(f"w must have shape ({self.p.Nr},)")
         loss = C.c_double()
         gU = np.zeros((self.p.Nr, self.p.Nt))
         gJ = np.zeros((max(self.p.Nb, 1), self.p.Nt))
@@ -274,6 +288,9 @@ class Solver:
         t_index = self.p.Nt - 1 if t_index is None else t_index
         wn = None if w_density is None else np.ascontiguousarray(np.asarray(w_density, dtype=np.float64))
         wd = None if w_docc is None else np.ascontiguousarray(np.asarray(w_docc, dtype=np.float64))
+        for nm, a in (("w_density", wn), ("w_docc", wd)):
+            if a is not None and a.shape != (self.p.Nr,):
+                raise ValueError(f"{nm} must have shape ({self.p.Nr},)")
         loss = C.c_double()
         gU = np.zeros((self.p.Nr, self.p.Nt))
         gJ = np.zeros((max(self.p.Nb, 1), self.p.Nt))
@@ -295,8 +312,10 @@ class Solver:
         return n, e, d
 
     def observables_device(self, n, ekin, docc):
-        self._check(self.lib.dyson_observables(self.h, C.c_void_p(n.data_ptr()), C.c_void_p(ekin.data_ptr()),
-                                               C.c_void_p(docc.data_ptr()), 1))
+        """(n, ekin, D) into float64 device tensors of Nr * Nt elements each."""
+        size, f64 = self.p.Nr * self.p.Nt, self._torch.float64
+        ptrs = [device_buffer(t, f64, size, self.device, nm) for t, nm in ((n, "n"), (ekin, "ekin"), (docc, "docc"))]
+        self._check(self.lib.dyson_observables(self.h, *ptrs, 1))
 
     def launch_count(self) -> int:
         return int(self.lib.dyson_launch_count(self.h))
@@ -324,20 +343,21 @@ class Solver:
         if out is None:
             out = torch.zeros((self.p.Nr, self.p.Nc, self.p.Nc), dtype=torch.complex128,
                               device=torch.device("cuda", self.device))
-        assert out.is_cuda and out.dtype == torch.complex128 and out.is_contiguous()
-        assert out.numel() == self.p.Nr * self.p.Nc * self.p.Nc
+        optr = device_buffer(out, torch.complex128, self.p.Nr * self.p.Nc * self.p.Nc, self.device, "out")
         rep = Report()
         rc = self.lib.dyson_local_greens(self.h, src.ctypes.data_as(C.POINTER(C.c_int32)), len(src), precision, tol,
-                                         max_sweeps, C.c_void_p(out.data_ptr()), C.byref(rep))
+                                         max_sweeps, optr, C.byref(rep))
         self._check(rc, ok=allow)
         return out, SolveResult(rc, rep.as_dict())
 
     def selfenergy_step(self, gloc, mix=0.7, sigma_tilde=None):
         """One self-energy step from the local Green's functions `gloc` (device [Nr, Nc, Nc]);
         installs the new local blocks and returns the convergence measure."""
+        n_el, c128 = self.p.Nr * self.p.Nc * self.p.Nc, self._torch.complex128
+        gptr = device_buffer(gloc, c128, n_el, self.device, "gloc")
+        st = device_buffer(sigma_tilde, c128, n_el, self.device, "sigma_tilde") if sigma_tilde is not None else None
         crit = C.c_double()
-        st = C.c_void_p(sigma_tilde.data_ptr()) if sigma_tilde is not None else None
-        self._check(self.lib.dyson_selfenergy_step(self.h, C.c_void_p(gloc.data_ptr()), mix, st, C.byref(crit)))
+        self._check(self.lib.dyson_selfenergy_step(self.h, gptr, mix, st, C.byref(crit)))
         return crit.value
 
     def set_anderson(self, depth: int):
@@ -391,7 +411,8 @@ class Batch:
         """sources[k]: block-column source sites of instance k; g_outs: None or per
         instance None / a complex128 device tensor [len(sources[k]), Nr, Nc, Nc]."""
         n = len(self.solvers)
-        assert len(sources) == n
+        if len(sources) != n:
+            raise ValueError(f"sources must list {n} instances")
         keep = [np.ascontiguousarray(np.asarray(s, dtype=np.int32)) for s in sources]
         ptrs = (C.POINTER(C.c_int32) * n)(*[k.ctypes.data_as(C.POINTER(C.c_int32)) for k in keep])
         counts = (C.c_int32 * n)(*[len(k) for k in keep])
@@ -402,9 +423,8 @@ class Batch:
                 if g is None:
                     vals.append(None)
                     continue
-                assert g.is_cuda and g.dtype == sv._torch.complex128 and g.is_contiguous()
-                assert g.numel() == len(k) * sv.p.Nr * sv.p.Nc * sv.p.Nc
-                vals.append(g.data_ptr())
+                vals.append(device_buffer(g, sv._torch.complex128, len(k) * sv.p.Nr * sv.p.Nc * sv.p.Nc, sv.device,
+                                          "g_outs[i]").value)
             gp = (C.c_void_p * n)(*vals)
         reps = (Report * n)()
         rc = self.lib.dyson_batch_solve(self.h, ptrs, counts, tol, max_sweeps, graph_sweeps, gp, reps)
