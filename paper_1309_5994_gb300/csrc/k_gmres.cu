@@ -145,89 +145,6 @@ __global__ void __launch_bounds__(GM_THREADS) k_gm_dots(const float* __restrict_
   }
 }
 
-// The same projections for every basis vector at once: h[n][i] += <Q_i[n], a[n] - b[n]>
-// for all i < nvec, and nrm0[n] += |a - b|^2 when nrm0 is given.  Each warp takes a site,
-// keeps its row of a - b in registers (E elements of each plane per lane, Nc <= 32 E)
-// and streams the basis rows past it, so a and b are read once instead of once per basis
-// vector.  Per site the FP32 lane sums are reduced in FP64 across the warp, as above.
-// grid: (ncol, site chunks); dynamic shared memory: (warps per block) x nvec double2.
-template <int E>
-__global__ void __launch_bounds__(GM_THREADS) k_gm_dots_all(const float* __restrict__ Q, size_t vsz, int nvec,
-                                                            const float* __restrict__ a, const float* __restrict__ b,
-                                                            int Nr, int Nc, int ncol, int sites_per_blk,
-                                                            double2* __restrict__ h, int hstride,
-                                                            double* __restrict__ nrm0,
-                                                            const double* __restrict__ after,
-                                                            const double* __restrict__ before) {
-  extern __shared__ double2 hsh[];   // [nwarps][nvec]
-  __shared__ double sh[GM_THREADS / 32];
-  const int n = blockIdx.x;
-  if (after && !reorth_needed(after, before, n)) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int e = threadIdx.x; e < nwarps * nvec; e += blockDim.x) hsh[e] = make_double2(0.0, 0.0);
-  __syncthreads();
-  const int s0 = blockIdx.y * sites_per_blk, s1 = min(Nr, s0 + sites_per_blk);
-  double sq = 0.0;
-  for (int s = s0 + warp; s < s1; s += nwarps) {
-    const size_t base = ((size_t)s * ncol + n) * 2 * Nc;
-    float wr[E], wi[E];
-    float ssq = 0.f;
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const int z = lane + 32 * k;
-      float xr = 0.f, xi = 0.f;
-      if (z < Nc) {
-        xr = a[base + z];
-        xi = a[base + Nc + z];
-        if (b) {
-          xr -= b[base + z];
-          xi -= b[base + Nc + z];
-        }
-      }
-      wr[k] = xr;
-      wi[k] = xi;
-      ssq = fmaf(xr, xr, fmaf(xi, xi, ssq));
-    }
-    sq += ssq;
-    for (int i = 0; i < nvec; ++i) {
-      const float* __restrict__ q = Q + (size_t)i * vsz + base;
-      float sre = 0.f, sim = 0.f;
-#pragma unroll
-      for (int k = 0; k < E; ++k) {
-        const int z = lane + 32 * k;
-        if (z < Nc) {
-          const float qre = q[z], qim = q[Nc + z];
-          sre = fmaf(qre, wr[k], fmaf(qim, wi[k], sre));    // conj(q) w
-          sim = fmaf(qre, wi[k], fmaf(-qim, wr[k], sim));
-        }
-      }
-      double dre = sre, dim = sim;
-      for (int o = 16; o > 0; o >>= 1) {
-        dre += __shfl_xor_sync(0xffffffffu, dre, o);
-        dim += __shfl_xor_sync(0xffffffffu, dim, o);
-      }
-      if (lane == 0) {
-        hsh[warp * nvec + i].x += dre;
-        hsh[warp * nvec + i].y += dim;
-      }
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nvec; i += blockDim.x) {
-    double re = 0.0, im = 0.0;
-    for (int w = 0; w < nwarps; ++w) {
-      re += hsh[w * nvec + i].x;
-      im += hsh[w * nvec + i].y;
-    }
-    atomicAdd(&h[(size_t)n * hstride + i].x, re);
-    atomicAdd(&h[(size_t)n * hstride + i].y, im);
-  }
-  if (nrm0) {
-    sq = block_sum(sq, sh);
-    if (threadIdx.x == 0) atomicAdd(&nrm0[n], sq);
-  }
-}
-
 // nrm[n] += |a[n]|^2; grid (Nr, ncol)
 __global__ void __launch_bounds__(GM_THREADS) k_gm_norm2(const float* __restrict__ a, int Nc, int ncol,
                                                          double* __restrict__ nrm) {
@@ -520,25 +437,6 @@ int gmres_inner_solve(dyson_ctx* c, int ncol, const float* r, float* x, int max_
   const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(c->Nr, 4096 / std::max(1, ncol)));
   const int sites_per_blk = (c->Nr + chunks - 1) / chunks;
   const int nchunk = (c->Nr + sites_per_blk - 1) / sites_per_blk;
-  // projections onto the first nvec basis vectors: all at once where a row of a - b fits in
-  // a warp's registers (Nc <= 768), else one basis vector per block
-  auto dots = [&](int nvec, const float* a, const float* b, double2* h, double* nrm0, const double* after,
-                  const double* before) {
-    const size_t shm = (size_t)(GM_THREADS / 32) * nvec * sizeof(double2);
-    const dim3 grid(ncol, nchunk);
-    if (Nc <= 256)
-      k_gm_dots_all<8><<<grid, GM_THREADS, shm, s>>>(st->Q, vsz, nvec, a, b, c->Nr, Nc, ncol, sites_per_blk, h,
-                                                     m + 1, nrm0, after, before);
-    else if (Nc <= 512)
-      k_gm_dots_all<16><<<grid, GM_THREADS, shm, s>>>(st->Q, vsz, nvec, a, b, c->Nr, Nc, ncol, sites_per_blk, h,
-                                                      m + 1, nrm0, after, before);
-    else if (Nc <= 768)
-      k_gm_dots_all<24><<<grid, GM_THREADS, shm, s>>>(st->Q, vsz, nvec, a, b, c->Nr, Nc, ncol, sites_per_blk, h,
-                                                      m + 1, nrm0, after, before);
-    else
-      k_gm_dots<<<dim3(nvec, ncol, nchunk), GM_THREADS, 0, s>>>(st->Q, vsz, a, b, c->Nr, Nc, ncol, sites_per_blk, h,
-                                                                m + 1, nrm0, after, before);
-  };
   const int cb = (ncol + 127) / 128;
   const size_t n4 = vsz / 4;
   const int lin_grid = (int)std::min<size_t>((n4 + 255) / 256, 152 * 16);
@@ -578,10 +476,14 @@ int gmres_inner_solve(dyson_ctx* c, int ncol, const float* r, float* x, int max_
       DY_CUDA(c, cudaMemsetAsync(st->nrm0, 0, ncol * sizeof(double), s));
       DY_CUDA(c, cudaMemsetAsync(st->nrm1, 0, ncol * sizeof(double), s));
       DY_CUDA(c, cudaMemsetAsync(st->nrm, 0, ncol * sizeof(double), s));
-      dots(j + 1, qj, st->u, st->h, st->nrm0, nullptr, nullptr);
+      k_gm_dots<<<dim3(j + 1, ncol, nchunk), GM_THREADS, 0, s>>>(st->Q, vsz, qj, st->u, c->Nr, Nc, ncol,
+                                                                 sites_per_blk, st->h, m + 1, st->nrm0, nullptr,
+                                                                 nullptr);
       k_gm_update<<<grid_el, GM_THREADS, 0, s>>>(st->Q, vsz, j + 1, st->h, m + 1, qj, st->u, st->w, Nc, ncol,
                                                   st->nrm1, nullptr, nullptr);
-      dots(j + 1, st->w, nullptr, st->h2, nullptr, st->nrm1, st->nrm0);
+      k_gm_dots<<<dim3(j + 1, ncol, nchunk), GM_THREADS, 0, s>>>(st->Q, vsz, st->w, nullptr, c->Nr, Nc, ncol,
+                                                                 sites_per_blk, st->h2, m + 1, nullptr, st->nrm1,
+                                                                 st->nrm0);
       k_gm_update<<<grid_el, GM_THREADS, 0, s>>>(st->Q, vsz, j + 1, st->h2, m + 1, st->w, nullptr, st->w, Nc, ncol,
                                                   st->nrm, st->nrm1, st->nrm0);
       k_gm_scale<<<grid_el, GM_THREADS, 0, s>>>(st->w, st->nrm, st->Q + (size_t)(j + 1) * vsz, Nc, ncol);
