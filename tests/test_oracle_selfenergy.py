@@ -271,3 +271,29 @@ def test_fixed_point_does_not_depend_on_where_the_real_branches_end():
     assert np.abs(St_s).max() > 1e-3
     assert np.abs(St_l[:, ix][:, :, ix] - St_s).max() < 1e-14
     assert np.abs(Gl_l[:, ix][:, :, ix] - Gl_s).max() < 1e-13
+
+
+def _particle_number_drift(dt, with_selfenergy):
+    """max_t N(t) - min_t N(t), N(t) = sum_i n_i(t) from the local Green's functions of a driven
+    2x2 lattice (U and J modulated) on t <= 0.6."""
+    Nt = int(round(0.6 / dt)) + 1
+    p = wl.small(L=2, Nt=Nt, Nm=8, dt=dt, beta=1.0, trap_c=0.3, U0=8.0, J0=0.5, aU=0.2, aJ=0.3, omega=5.0)
+    S = dyson.setup(p)
+    blocks = S.Lam
+    if with_selfenergy:
+        blocks = se.self_consistent(p, mix=0.7, delta_sc=1e-10, max_iter=80)[0]
+    g = se.local_greens(S, blocks)
+    N = np.array([sum(np.real(-1j * g[i][k, k]) for i in range(S.Nr)) for k in range(Nt)])
+    return N.max() - N.min()
+
+
+def test_self_consistency_conserves_particle_number_as_dt_vanishes():
+    """Under a drive the total particle number N = sum_i n_i(t) is constant (Sec. V): the
+    self-consistent solution's drift falls with the time step (about first order), while the
+    lattice Dyson equation with Lambda alone (no self-energy) keeps a drift that does not
+    vanish, so the conservation comes from the self-energy step."""
+    sc = [_particle_number_drift(dt, True) for dt in (0.1, 0.05)]
+    lam = [_particle_number_drift(dt, False) for dt in (0.1, 0.05)]
+    assert sc[1] < 0.45 * sc[0]
+    assert lam[1] > 0.6 * lam[0]
+    assert sc[1] < 0.35 * lam[1]
