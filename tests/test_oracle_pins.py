@@ -247,3 +247,38 @@ def test_matsubara_block_converges_to_continuum_hubbard_one():
         errs.append(np.abs(got - ref).max())
     assert errs[2] < 0.02
     assert 1.7 < errs[0] / errs[1] < 2.3 and 1.7 < errs[1] / errs[2] < 2.3
+
+
+def _equilibrium_and_anticommutator(dt, Nm, T=0.6):
+    """On a 3x3 trapped lattice: (i) the spread over t of G_44(t + 0.2, t) without a drive,
+    (ii) the largest deviation of G^>_ij(t, t) - G^<_ij(t, t) from -i delta_ij with a drive."""
+    Nt = int(round(T / dt)) + 1
+    lag = int(round(0.2 / dt))
+    S = dyson.setup(wl.small(L=3, Nt=Nt, Nm=Nm, dt=dt, beta=1.0, trap_c=0.3, U0=8.0, J0=1.0))
+    G = dyson.dense_solve(S, dyson.rhs_block_columns(S, [4]))
+    vals = np.array([G[4, k + lag, k] for k in range(Nt - lag)])
+    spread = np.abs(vals - vals[0]).max()
+    S = dyson.setup(wl.small(L=3, Nt=Nt, Nm=Nm, dt=dt, beta=1.0, trap_c=0.3, U0=8.0, J0=1.0,
+                             aU=0.2, aJ=0.3, omega=5.0))
+    G = dyson.dense_solve(S, dyson.rhs_block_columns(S, range(S.Nr)))
+    Nc, err = S.Nc, 0.0
+    for k in range(Nt):
+        zf, zb = k, 2 * Nt - 1 - k           # forward diagonal: lesser; backward diagonal: greater
+        for j in range(S.Nr):
+            d = G[:, zb, j * Nc + zb] - G[:, zf, j * Nc + zf]
+            d[j] += 1j
+            err = max(err, np.abs(d).max())
+    return spread, err
+
+
+def test_equilibrium_translation_invariance_and_equal_time_anticommutator():
+    """Without a drive G(t + s, t) does not depend on t, and at equal times
+    G^> - G^< = -i delta_ij (the canonical anticommutator), both of the continuum theory.
+    On the discretised contour both hold to first order: the deviations fall by about 2
+    when dt and dtau are halved (the translation invariance needs dtau refined as well: the
+    imaginary branch carries the initial correlations)."""
+    r = [_equilibrium_and_anticommutator(dt, Nm) for dt, Nm in ((0.1, 8), (0.05, 16), (0.025, 32))]
+    spread = [x[0] for x in r]
+    anti = [x[1] for x in r]
+    assert spread[2] < 0.5 * spread[0] and spread[1] / spread[2] > 1.5
+    assert 1.7 < anti[0] / anti[1] < 2.3 and 1.7 < anti[1] / anti[2] < 2.3
