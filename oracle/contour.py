@@ -10,6 +10,11 @@ the grid below is this project's reading of it:
 
 Contour order is index order.  Quadrature weights are the left rectangle rule
 of the contour measure dz: +dt forward, -dt backward, -i*dtau imaginary.
+
+Parity: the grid, the weights and the equal-point order are pinned through what
+they produce: the brute-force atomic trace, the exact independence of the
+contour end, and the first-order approach of the lattice function to the
+continuum sum rules (tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 

@@ -23,6 +23,13 @@ momentum-space check the paper uses in Sec. IV.D).
 
 Reading: the hopping on the imaginary branch is J(t=0), the value of the
 initial equilibrium Hamiltonian.
+
+Parity: pinned in tests/test_oracle_pins.py and tests/test_oracle_gmres.py: the
+series, the dense solve and GMRES agree (1e-12 to 1e-13), the dense solve equals
+the sine-mode diagonalisation of homogeneous lattices, J = 0 returns Lambda, the
+result does not depend on where the real branches end, G_ii has the C4v symmetry,
+and the free-fermion (U = 0), Hubbard-I Matsubara, time-translation and
+anticommutator limits of the continuum are reached at first order.
 """
 from __future__ import annotations
 

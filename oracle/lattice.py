@@ -4,6 +4,10 @@ Sites i = y*Lx + x with open boundaries; the trap is V_trap(r) = c*|r|^2 about
 the geometric centre of the lattice (Sec. V.A gives V_trap proportional to |r|^2);
 eps_i = V_trap(r_i) - U_i(0)/2 - mu (Eq. onsitelevels).  Bonds are listed
 horizontal first, then vertical.
+
+Parity: the neighbour lists and levels are pinned by the open-boundary sine-mode
+solve of homogeneous lattices and the exact C4v symmetry of G_ii in a centred
+trap (tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 

@@ -19,6 +19,10 @@ the sign of nearest-neighbour elements.  The kinetic-energy formula of
 Sec. III.A is written for Eq. (model), so on the solved G it carries the factor
 -i instead of +i; with it, Eq. (docc) holds for the solved G (checked in the
 tests at U = 0, where the double-occupancy term drops out).
+
+Parity: pinned at J = 0 (n = rho_s + rho_d, D at its exact discrete value) and at
+U = 0 (the free-fermion densities and the equation of motion dG/dt = eps n + ekin,
+both at first order in dt) in tests/test_oracle_pins.py.
 """
 from __future__ import annotations
 

@@ -60,8 +60,9 @@ to dtau, dt -> 0, is that of exact diagonalisation on the imaginary branch and o
 the real-time branch (G^>(t, 0)), which the lattice Dyson equation without
 self-energy misses; and the self-consistent fixed point restricted to the times
 of a shorter contour is that of the shorter contour to rounding, the discrete
-causality that a wrong branch order or weight would break
-(tests/test_oracle_selfenergy.py).
+causality that a wrong branch order or weight would break; and under a drive the
+self-consistent particle number sum_i n_i(t) becomes constant as dt -> 0, which
+Lambda alone does not give (tests/test_oracle_selfenergy.py).
 """
 from __future__ import annotations
 
