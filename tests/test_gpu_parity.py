@@ -420,3 +420,38 @@ def test_config2_sampled_columns_mixed(torch_cuda, lib):
     Gn, _, _ = dyson.neumann_solve(S, Bn, tol=1e-15, max_sweeps=400)
     n_ref = np.array([np.real(-1j * Gn[i, k, k]) for k in range(p.Nt)])
     assert np.abs(n[i] - n_ref).max() / np.abs(n_ref).max() < 1e-6
+
+
+def test_config2_bench_launch_shape_sampled_columns(torch_cuda, lib):
+    """The benchmark's launch configuration on its workload: 16 block columns of the 16x16,
+    Nc = 256 lattice in one chunk (single-CTA sweep variant, support truncation on, as the
+    tuner picks), mixed precision at the benchmark's tolerance 1e-6, sources 112..127 (one
+    of its batches).  Sampled vector columns of four block columns, and the densities of two
+    sources at three times, against the oracle's complex128 series; bound 1e-6 relative."""
+    torch = torch_cuda
+    from paper_1309_5994_gb300 import binding
+    p = wl.config2()
+    S = dyson.setup(p)
+    s = _solver(p)
+    s.set_sweep_variant(binding.SWEEP_SINGLE_CTA)
+    s.set_chunk(16)
+    sources = list(range(112, 128))
+    g = torch.empty((len(sources), p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda:0")
+    res = s.solve(sources, precision=binding.PREC_TF32X3_F64REF, tol=1e-6, max_sweeps=400, g_out=g)
+    assert res.report["chunks"] == 1
+    rng = np.random.default_rng(11)
+    picks = [(q, int(z)) for q in (0, 5, 10, 15) for z in rng.choice(p.Nc, 2, replace=False)]
+    dens = [(q, z) for q in (0, 7) for z in (0, p.Nt // 2, p.Nt - 1)]
+    allp = picks + dens
+    got = torch.stack([g[q, :, :, z] for q, z in allp], dim=-1).cpu().numpy()     # [Nr, Nc, columns]
+    del g
+    B = dyson.rhs_vector_columns(S, [(sources[q], z) for q, z in allp])
+    ref, _, _ = dyson.neumann_solve(S, B, tol=1e-15, max_sweeps=400)
+    assert dyson.residual(S, B, ref) < 1e-11
+    k = len(picks)
+    assert _rel(got[:, :, :k], ref[:, :, :k]) < 1e-6           # max-norm error relative to max |G|
+    n, _, _ = s.observables()
+    for c, (q, z) in enumerate(dens, start=len(picks)):
+        i = sources[q]
+        n_ref = np.real(-1j * ref[i, z, c])
+        assert abs(n[i, z] - n_ref) < 1e-6 * abs(n_ref)
