@@ -456,8 +456,6 @@ int dyson_init(dyson_ctx** out, const dyson_lattice* L, const dyson_contour* C, 
       delete c;
       return fail_noctx(DYSON_ERR_INVALID_ARG, "J table holds a non-finite value");
     }
-  if (const char* e = std::getenv("DYSON_MAX_REFINEMENTS")) c->max_refinements = std::max(1, atoi(e));
-  if (const char* e = std::getenv("DYSON_NO_TC")) c->tc_enabled = !(e[0] == '1');
   if (const char* e = std::getenv("DYSON_NO_OZ")) c->oz_enabled = !(e[0] == '1');
   if (const char* e = std::getenv("DYSON_TC_PAIR")) c->tc_variant = (e[0] == '1') ? DYSON_SWEEP_CTA_PAIR : 0;
 

@@ -120,7 +120,7 @@ struct dyson_ctx {
 
   bool lam32_built = false;
   bool lam_split_built = false;
-  bool tc_enabled = true;            // 3xTF32 tcgen05 sweep allowed (DYSON_NO_TC=1 disables)
+  bool tc_enabled = true;            // 3xTF32 tcgen05 sweep allowed where the contour fits it
   bool use_tc = false;               // chosen for the current solve
   int tc_variant = 0;                // DYSON_SWEEP_SINGLE_CTA or DYSON_SWEEP_CTA_PAIR
   int max_refinements = 12;
