@@ -456,8 +456,6 @@ int dyson_init(dyson_ctx** out, const dyson_lattice* L, const dyson_contour* C, 
       delete c;
       return fail_noctx(DYSON_ERR_INVALID_ARG, "J table holds a non-finite value");
     }
-  if (const char* e = std::getenv("DYSON_NO_OZ")) c->oz_enabled = !(e[0] == '1');
-  if (const char* e = std::getenv("DYSON_TC_PAIR")) c->tc_variant = (e[0] == '1') ? DYSON_SWEEP_CTA_PAIR : 0;
 
   // neighbour slots (+x, -x, +y, -y) with their bond indices
   std::vector<int> nbr((size_t)c->Nr * 4, -1), nbond((size_t)c->Nr * 4, -1);
@@ -568,7 +566,6 @@ int64_t chunk_columns(dyson_ctx* c, int precision, int64_t unit, int64_t want, s
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 0;
   const double budget = 0.85 * (double)(free_b + c->work_bytes);
   int64_t cols = (int64_t)(budget / col_bytes);
-  if (const char* e = std::getenv("DYSON_CHUNK")) cols = std::min<int64_t>(cols, (int64_t)std::max(1, atoi(e)) * unit);
   if (c->chunk_override > 0) cols = std::min<int64_t>(cols, (int64_t)c->chunk_override * unit);
   cols = std::min<int64_t>(cols, want);
   cols = std::min<int64_t>(cols, (int64_t)1 << 24);

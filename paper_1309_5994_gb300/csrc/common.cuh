@@ -153,7 +153,7 @@ struct dyson_ctx {
   size_t act_bytes = 0;
   void* se = nullptr;                // self-energy step state (atomic G0, its pseudo-inverse, mixed T)
   bool se_installed = false;         // Lambda holds the local block of a self-energy step
-  bool oz_enabled = true;            // DYSON_NO_OZ=1 keeps the FP64 CUDA-core residual
+  bool oz_enabled = true;            // split-product residual allowed where 2 Nc <= 512
   bool use_oz = false;               // chosen for the current solve
 
   std::string err;
