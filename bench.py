@@ -64,7 +64,7 @@ def parse():
     return ap.parse_args()
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_config2_16cols.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_trapped16x16_16cols.json")
 
 
 def load_traffic():
@@ -258,7 +258,7 @@ def batched_uneven_leg(args, dev, stream):
     import torch
     import workloads as wl
     from paper_1309_5994_gb300 import binding
-    problems = wl.config4(count=args.uneven_instances)
+    problems = wl.uneven_batch(count=args.uneven_instances)
     solvers = []
     for p in problems:
         s = binding.Solver(p, device=dev.index, stream=stream)
@@ -309,7 +309,7 @@ def driven_leg(args, dev, stream):
     import torch
     import workloads as wl
     from paper_1309_5994_gb300 import binding
-    p = wl.config3()
+    p = wl.driven_32x32_nc384()
     s = binding.Solver(p, device=dev.index, stream=stream)
     s.build_sigma()
     src = [527]
@@ -346,7 +346,7 @@ def wedge_leg(args, dev, stream, tuning):
     import torch
     import workloads as wl
     from paper_1309_5994_gb300 import binding
-    p = wl.config2()
+    p = wl.trapped_16x16_nc256()
     s = binding.Solver(p, device=dev.index, stream=stream)
     s.set_sweep_variant(tuning["sweep_variant"])
     s.set_chunk(tuning["chunk_block_columns"])
@@ -375,7 +375,7 @@ def run_reference(args, rank, world):
     import numpy as np
     import workloads as wl
     from oracle import dyson
-    p = wl.config2()
+    p = wl.trapped_16x16_nc256()
     S = dyson.setup(p)
     ncols = 16
     times = []
@@ -409,8 +409,8 @@ def run_gb300(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    p = wl.config2() if args.lattice == 16 else wl.uniform_problem(
-        f"c2_L{args.lattice}_Nc256", args.lattice, 112, 32, 0.05, 2.0, 0.0, 0.02, 20.0, 1.0)
+    p = wl.trapped_16x16_nc256() if args.lattice == 16 else wl.uniform_problem(
+        f"trapped_L{args.lattice}_Nc256", args.lattice, 112, 32, 0.05, 2.0, 0.0, 0.02, 20.0, 1.0)
     stream = torch.cuda.Stream(device=dev)
     solver = binding.Solver(p, device=local, stream=stream)
     PREC = binding.PREC_TF32X3_F64REF
@@ -577,7 +577,7 @@ def run_gb300(args, rank, world, local):
             if args.uneven_instances > 0:
                 extras["batched_uneven"] = batched_uneven_leg(args, dev, stream)
             if not args.no_driven:
-                extras["driven_config3"] = driven_leg(args, dev, stream)
+                extras["driven_32x32"] = driven_leg(args, dev, stream)
             extras["c4v_wedge_all_sources"] = wedge_leg(args, dev, stream, tuning)
             if not args.no_selfenergy:
                 extras["selfenergy_loop"] = selfenergy_leg(args, dev, stream)

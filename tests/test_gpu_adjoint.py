@@ -136,12 +136,12 @@ def test_autograd_amplitude_gradient(torch_cuda, lib):
     assert abs(s.grad.item() - float(np.sum(gU * dU) + np.sum(gJ * dJ))) < 1e-10 * max(1.0, abs(s.grad.item()))
 
 
-def test_config5_amplitude_gradient_matches_finite_differences(torch_cuda, lib):
-    """24x24 lattice, Nc = 256, config-3 drive scaled by s: d/ds of
+def test_driven_24x24_amplitude_gradient_matches_finite_differences(torch_cuda, lib):
+    """24x24 lattice, Nc = 256, the 32x32 lattice's drive scaled by s: d/ds of
     sum_i w_i n_i(t_final) from the adjoint (chain rule through the U and J
     tables) against central differences with h = 1e-4, to 1e-5 relative."""
-    w = wl.config5_weights()
-    base = wl.config5(1.0)
+    w = wl.loss_weights()
+    base = wl.driven_24x24_nc256(1.0)
     s = _solver(base)
     L0, gU, gJ, res = s.adjoint(w, precision=1, tol=1e-11)
     dU, dJ = wl.drive_derivative_tables(base)
@@ -149,7 +149,7 @@ def test_config5_amplitude_gradient_matches_finite_differences(torch_cuda, lib):
     h = 1e-4
     vals = []
     for amp in (1.0 + h, 1.0 - h):
-        sp = _solver(wl.config5(amp))
+        sp = _solver(wl.driven_24x24_nc256(amp))
         vals.append(sp.adjoint(w, precision=1, tol=1e-11)[0])
         sp.close()
     fd = (vals[0] - vals[1]) / (2 * h)

@@ -107,13 +107,13 @@ def test_batch_rejects_bad_members(torch_cuda, lib):
     b.close()
 
 
-def test_uneven_batch_config4_sampled(torch_cuda, lib):
+def test_uneven_batch_of_64_sampled(torch_cuda, lib):
     """Six instances of the seeded uneven batch (L in 8..24, Nc in {128, 192, 256}),
     one block column each, solved in one batch: sampled vector columns and the
     source-site densities against the oracle's complex128 series."""
     torch = torch_cuda
     from paper_1309_5994_gb300 import binding
-    allp = wl.config4()
+    allp = wl.uneven_batch()
     problems = [p for p in allp if p.Lx <= 12][:6]                         # the oracle's share stays small
     assert {p.Nc for p in problems} == {128, 192, 256}
     solvers, _ = _solvers(torch, problems)

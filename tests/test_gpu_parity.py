@@ -59,8 +59,8 @@ def test_sigma_matches_oracle(torch_cuda, lib, kw):
     assert _rel(got, S.Lam) < 1e-13
 
 
-def test_sigma_config1(torch_cuda, lib):
-    p = wl.config1()
+def test_sigma_trapped_4x4(torch_cuda, lib):
+    p = wl.trapped_4x4_nc64()
     S = dyson.setup(p)
     s = _solver(p)
     assert _rel(s.sigma(), S.Lam) < 1e-13
@@ -232,8 +232,8 @@ def test_autotune_picks_a_measured_candidate_and_solves(torch_cuda, lib):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_config1_all_columns_and_observables(torch_cuda, lib, prec):
-    p = wl.config1()
+def test_trapped_4x4_all_columns_and_observables(torch_cuda, lib, prec):
+    p = wl.trapped_4x4_nc64()
     S = dyson.setup(p)
     sources = list(range(p.Nr))
     ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
@@ -357,12 +357,12 @@ def test_forced_gmres_matches_dense(torch_cuda, lib, kw):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
 
-def test_config3_sampled_columns_mixed_gmres(torch_cuda, lib):
+def test_driven_32x32_sampled_columns_mixed_gmres(torch_cuda, lib):
     """32x32 lattice, driven, Nc = 384, one block column in mixed precision: the
     FP32 series cannot serve here (its partial sums peak ~2e7 above the result),
     so AUTO refines with GMRES.  Sampled vector columns against the oracle's
     complex128 GMRES (residual 1e-12)."""
-    p = wl.config3()
+    p = wl.driven_32x32_nc384()
     S = dyson.setup(p)
     s = _solver(p)
     src = 527
@@ -376,7 +376,7 @@ def test_config3_sampled_columns_mixed_gmres(torch_cuda, lib):
         assert _rel(got[0][:, :, z], ref[:, :, c]) < 1e-7
 
 
-def test_config3_sampled_columns_fp64(torch_cuda, lib):
+def test_driven_32x32_sampled_columns_fp64(torch_cuda, lib):
     """32x32 lattice, driven, Nc = 384: one block column in FP64, sampled vector
     columns against the oracle's complex128 series run for the same 130 sweeps.
 
@@ -385,7 +385,7 @@ def test_config3_sampled_columns_fp64(torch_cuda, lib):
     out near 5e-8 after ~105 sweeps and never reaches a 1e-12 tolerance): the
     two are compared at 1e-7, and NOT_CONVERGED is the expected status.
     """
-    p = wl.config3()
+    p = wl.driven_32x32_nc384()
     S = dyson.setup(p)
     s = _solver(p)
     src = 527                                            # near the trap centre
@@ -398,10 +398,10 @@ def test_config3_sampled_columns_fp64(torch_cuda, lib):
         assert _rel(got[0][:, :, z], ref[:, :, c]) < 1e-7
 
 
-def test_config2_sampled_columns_mixed(torch_cuda, lib):
+def test_trapped_16x16_sampled_columns_mixed(torch_cuda, lib):
     """16x16 lattice, Nc = 256, the benchmark's launch shape: sampled vector
     columns of two block columns against the oracle's complex128 series."""
-    p = wl.config2()
+    p = wl.trapped_16x16_nc256()
     S = dyson.setup(p)
     s = _solver(p)
     sources = [0, 119]                                       # a corner and a near-centre site
@@ -422,7 +422,7 @@ def test_config2_sampled_columns_mixed(torch_cuda, lib):
     assert np.abs(n[i] - n_ref).max() / np.abs(n_ref).max() < 1e-6
 
 
-def test_config2_bench_launch_shape_sampled_columns(torch_cuda, lib):
+def test_trapped_16x16_bench_launch_shape_sampled_columns(torch_cuda, lib):
     """The benchmark's launch configuration on its workload: 16 block columns of the 16x16,
     Nc = 256 lattice in one chunk (single-CTA sweep variant, support truncation on, as the
     tuner picks), mixed precision at the benchmark's tolerance 1e-6, sources 112..127 (one
@@ -430,7 +430,7 @@ def test_config2_bench_launch_shape_sampled_columns(torch_cuda, lib):
     sources at three times, against the oracle's complex128 series; bound 1e-6 relative."""
     torch = torch_cuda
     from paper_1309_5994_gb300 import binding
-    p = wl.config2()
+    p = wl.trapped_16x16_nc256()
     S = dyson.setup(p)
     s = _solver(p)
     s.set_sweep_variant(binding.SWEEP_SINGLE_CTA)

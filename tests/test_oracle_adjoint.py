@@ -50,7 +50,7 @@ def test_adjoint_gradients_match_finite_differences():
 
 
 def test_amplitude_gradient_is_the_chain_rule():
-    """d/ds of the config-5 style drive equals sum(gU dU/ds) + sum(gJ dJ/ds)."""
+    """d/ds of the scaled drive (U and J modulations times s) equals sum(gU dU/ds) + sum(gJ dJ/ds)."""
     def make(s):
         return wl.small(L=2, Ly=2, Nt=6, Nm=4, dt=0.05, trap_c=0.2, U0=20.0, aU=0.1, aJ=0.2, omega=20.0, amp=s)
 

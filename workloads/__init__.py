@@ -103,26 +103,26 @@ def drive_derivative_tables(p: Problem):
 
 
 # --------------------------------------------------------------------------
-# The five workloads (all synthetic, shaped like the paper's Sec. V runs).
+# The workloads (all synthetic, shaped like the paper's Sec. V runs).
 # --------------------------------------------------------------------------
 
-def config1() -> Problem:
+def trapped_4x4_nc64() -> Problem:
     """4x4 lattice, U=20, J=1, trap 0.5|r|^2, beta=1, Nt=24, Nm=16, dt=0.05 (Nc=64)."""
-    return uniform_problem("c1_L4_Nc64", 4, 24, 16, 0.05, 1.0, 0.0, 0.5, 20.0, 1.0)
+    return uniform_problem("trapped_L4_Nc64", 4, 24, 16, 0.05, 1.0, 0.0, 0.5, 20.0, 1.0)
 
 
-def config2() -> Problem:
+def trapped_16x16_nc256() -> Problem:
     """16x16 lattice, U=20, J=1, trap 0.02|r|^2, beta=2, Nt=112, Nm=32, dt=0.05 (Nc=256)."""
-    return uniform_problem("c2_L16_Nc256", 16, 112, 32, 0.05, 2.0, 0.0, 0.02, 20.0, 1.0)
+    return uniform_problem("trapped_L16_Nc256", 16, 112, 32, 0.05, 2.0, 0.0, 0.02, 20.0, 1.0)
 
 
-def config3() -> Problem:
+def driven_32x32_nc384() -> Problem:
     """32x32 lattice, U(t)=20(1+0.1 sin 20t), J(t)=1-0.2 sin 20t, trap 0.005|r|^2, beta=2, Nc=384."""
-    return uniform_problem("c3_L32_Nc384_driven", 32, 160, 64, 0.05, 2.0, 0.0, 0.005, 20.0, 1.0,
+    return uniform_problem("driven_L32_Nc384", 32, 160, 64, 0.05, 2.0, 0.0, 0.005, 20.0, 1.0,
                            aU=0.1, aJ=0.2, omega=20.0)
 
 
-def config4(seed: int = 1309, count: int = 64) -> List[Problem]:
+def uneven_batch(seed: int = 1309, count: int = 64) -> List[Problem]:
     """Uneven batch: L~U{8..24}, Nc~{128,192,256} (Nm=Nc/4), U~U[12,30], c~U[0.005,0.05], phase~U[0,2pi)."""
     rng = np.random.default_rng(seed)
     out = []
@@ -134,18 +134,18 @@ def config4(seed: int = 1309, count: int = 64) -> List[Problem]:
         ph = float(rng.uniform(0.0, 2.0 * np.pi))
         Nm = Nc // 4
         Nt = (Nc - Nm) // 2
-        out.append(uniform_problem(f"c4_{n:02d}_L{L}_Nc{Nc}", L, Nt, Nm, 0.05, 2.0, 0.0, c, U0, 1.0,
+        out.append(uniform_problem(f"uneven_{n:02d}_L{L}_Nc{Nc}", L, Nt, Nm, 0.05, 2.0, 0.0, c, U0, 1.0,
                                    aU=0.1, aJ=0.2, omega=20.0, phase=ph))
     return out
 
 
-def config5(amp: float = 1.0) -> Problem:
-    """24x24 lattice, Nt=96, Nm=64 (Nc=256), config-3 drive scaled by the amplitude `amp`."""
-    return uniform_problem("c5_L24_Nc256_adjoint", 24, 96, 64, 0.05, 2.0, 0.0, 0.005, 20.0, 1.0,
+def driven_24x24_nc256(amp: float = 1.0) -> Problem:
+    """24x24 lattice, Nt=96, Nm=64 (Nc=256), drive of the 32x32 lattice scaled by the amplitude `amp`."""
+    return uniform_problem("driven_L24_Nc256", 24, 96, 64, 0.05, 2.0, 0.0, 0.005, 20.0, 1.0,
                            aU=0.1, aJ=0.2, omega=20.0, amp=amp)
 
 
-def config5_weights(seed: int = 5, Nr: int = 576) -> np.ndarray:
+def loss_weights(seed: int = 5, Nr: int = 576) -> np.ndarray:
     """Site weights w_i ~ U[0,1] of the adjoint loss sum_i w_i n_i(t_final)."""
     return np.random.default_rng(seed).uniform(0.0, 1.0, size=Nr)
 
