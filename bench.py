@@ -572,15 +572,16 @@ def run_gb300(args, rank, world, local):
             extras["rel_err_vs_plain_f64"] = {"reference": "FP64 series to 1e-12", "G": gerr, "G_ii": gii_err,
                                               "density": nerr, "within_1e-6": bool(max(gii_err, nerr) <= 1e-6)}
             del g64, gmx
+            # the single-GPU legs run at N = 1 only: with more ranks every GPU would wait for them
             if world == 1:
                 extras["cpu_baseline"] = cpu_baseline(p, args.cpu_columns, args.tol)
-            if args.uneven_instances > 0:
-                extras["batched_uneven"] = batched_uneven_leg(args, dev, stream)
-            if not args.no_driven:
-                extras["driven_32x32"] = driven_leg(args, dev, stream)
-            extras["c4v_wedge_all_sources"] = wedge_leg(args, dev, stream, tuning)
-            if not args.no_selfenergy:
-                extras["selfenergy_loop"] = selfenergy_leg(args, dev, stream)
+                if args.uneven_instances > 0:
+                    extras["batched_uneven"] = batched_uneven_leg(args, dev, stream)
+                if not args.no_driven:
+                    extras["driven_32x32"] = driven_leg(args, dev, stream)
+                extras["c4v_wedge_all_sources"] = wedge_leg(args, dev, stream, tuning)
+                if not args.no_selfenergy:
+                    extras["selfenergy_loop"] = selfenergy_leg(args, dev, stream)
 
     if rank != 0:
         return
