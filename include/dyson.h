@@ -31,6 +31,14 @@
  * caller owns every pointer it passes in; none is retained after a call
  * returns.  All device work is ordered on the stream given to dyson_init.
  *
+ * Threads and streams: a context is not thread-safe; calls on one context must
+ * not overlap.  Distinct contexts may be used from distinct threads.  Every call
+ * on a context (or batch) that computes returns only after its work on the
+ * context's stream has finished (results written), so the caller needs no extra
+ * synchronisation before reading them; device buffers the caller passes must not
+ * be written by other streams while a call runs.  dyson_extrapolate_dt, which
+ * takes no context, is asynchronous on the stream it is given.
+ *
  * Errors: every int-returning call returns DYSON_OK (0) or a negative
  * DYSON_ERR_* code and never throws; dyson_last_error() describes the last
  * failure of a context.  No call falls back to a CPU implementation.
