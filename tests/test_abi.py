@@ -69,4 +69,13 @@ def test_init_rejects_bad_arguments_without_touching_a_gpu(libpath):
     lat = binding.Lattice(2, 2)
     con = binding.Contour(4, 4, -0.1, 1.0)
     assert lib.dyson_init(C.byref(h), C.byref(lat), C.byref(con), C.byref(trap), C.byref(drv), 0, None) == -1
+    # the largest sizes: 65535 sites, a contour of 2048 points
+    big = binding.Lattice(256, 256)
+    con = binding.Contour(4, 4, 0.1, 1.0)
+    assert lib.dyson_init(C.byref(h), C.byref(big), C.byref(con), C.byref(trap), C.byref(drv), 0, None) == -1
+    long = binding.Contour(1000, 49, 0.1, 1.0)
+    assert lib.dyson_init(C.byref(h), C.byref(lat), C.byref(long), C.byref(trap), C.byref(drv), 0, None) == -1
+    assert b"2048" in lib.dyson_last_error(None)
+    nan_trap = binding.Trap(float("nan"), 0.0)
+    assert lib.dyson_init(C.byref(h), C.byref(lat), C.byref(con), C.byref(nan_trap), C.byref(drv), 0, None) == -1
     assert lib.dyson_build_sigma(None) == -1

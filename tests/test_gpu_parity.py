@@ -270,6 +270,10 @@ def test_error_codes(torch_cuda, lib):
     assert e.value.code == -1                               # source out of range
     r = s.solve([0], max_sweeps=1, allow=(-3,))
     assert r.status == -3 and r.report["sweeps"] == 1       # not converged, results still written
+    for call in (lambda: s.solve([]), lambda: s.local_greens([])):
+        with pytest.raises(binding.DysonError) as e:        # no source site
+            call()
+        assert e.value.code == -1
 
 
 def test_slow_series_reports_not_converged(torch_cuda, lib):
