@@ -22,7 +22,9 @@ tests at U = 0, where the double-occupancy term drops out).
 
 Parity: pinned at J = 0 (n = rho_s + rho_d, D at its exact discrete value) and at
 U = 0 (the free-fermion densities and the equation of motion dG/dt = eps n + ekin,
-both at first order in dt) in tests/test_oracle_pins.py.
+both at first order in dt) in tests/test_oracle_pins.py, and at U, J != 0 by the
+O(J^2) double occupancy of the self-consistent Hubbard dimer against exact
+diagonalisation (tests/test_oracle_selfenergy.py).
 """
 from __future__ import annotations
 
