@@ -12,6 +12,8 @@ from oracle import atomic, contour, dyson, observables
 from oracle import extrapolate as ex
 from oracle import selfenergy as se
 
+from dimer_ed import dimer_fock, dimer_greater_exact, dimer_matsubara_exact, dimer_spectrum
+
 
 @pytest.fixture(scope="module")
 def grid():
@@ -135,52 +137,6 @@ def test_self_consistency_converges_to_a_fixed_point():
     assert np.abs(G2 - se.local_greens(S, S.Lam)).max() > 1e-4
 
 
-def _dimer_fock():
-    """c_1up, c_1dn, c_2up, c_2dn on the 16 states of two sites (Jordan-Wigner)."""
-    a = np.array([[0.0, 1.0], [0.0, 0.0]])
-    Z = np.diag([1.0, -1.0])
-    I = np.eye(2)
-    ops = []
-    for k in range(4):
-        m = np.array([[1.0]])
-        for j in range(4):
-            m = np.kron(m, Z if j < k else (a if j == k else I))
-        ops.append(m)
-    return ops
-
-
-def _dimer_spectrum(U, J, beta):
-    """Eigenpairs of the Hubbard dimer (eps = -U/2, hopping J), its thermal state and c_1up."""
-    c1u, c1d, c2u, c2d = _dimer_fock()
-    n = lambda c: c.T @ c
-    H = -U / 2 * (n(c1u) + n(c1d) + n(c2u) + n(c2d)) + U * (n(c1u) @ n(c1d) + n(c2u) @ n(c2d))
-    H = H + J * (c1u.T @ c2u + c2u.T @ c1u + c1d.T @ c2d + c2d.T @ c1d)
-    w, V = np.linalg.eigh(H)
-    w = w - w.min()
-    rho = V @ np.diag(np.exp(-beta * w)) @ V.T
-    return w, V, rho / np.trace(rho), c1u
-
-
-def _dimer_matsubara_exact(U, J, beta, taus):
-    """-i <c_1up(tau) c_1up^+(0)> of the Hubbard dimer by exact diagonalisation."""
-    w, V, rho, c = _dimer_spectrum(U, J, beta)
-    out = []
-    for t in taus:
-        c_t = V @ np.diag(np.exp(t * w)) @ V.T @ c @ V @ np.diag(np.exp(-t * w)) @ V.T
-        out.append(-1j * np.trace(rho @ c_t @ c.T))
-    return np.array(out)
-
-
-def _dimer_greater_exact(U, J, beta, ts):
-    """G^>(t, 0) = -i <c_1up(t) c_1up^+(0)> of the Hubbard dimer by exact diagonalisation."""
-    w, V, rho, c = _dimer_spectrum(U, J, beta)
-    out = []
-    for t in ts:
-        c_t = V @ np.diag(np.exp(1j * t * w)) @ V.T @ c @ V @ np.diag(np.exp(-1j * t * w)) @ V.T
-        out.append(-1j * np.trace(rho @ c_t @ c.T))
-    return np.array(out)
-
-
 def test_second_order_term_is_that_of_exact_diagonalisation():
     """The point of the self-energy step: the strong-coupling expansion to second order in J.
     On the Hubbard dimer the O(J^2) coefficient of the self-consistent local Green's function
@@ -212,7 +168,7 @@ def test_second_order_term_is_that_of_exact_diagonalisation():
     sc = sum(wb * c for wb, c in zip(w, c2_sc))
     hi = sum(wb * c for wb, c in zip(w, c2_hi))
     taus = np.arange(Nm0) * beta / Nm0
-    exact = (_dimer_matsubara_exact(U, h, beta, taus) - _dimer_matsubara_exact(U, 0.0, beta, taus)) / h ** 2
+    exact = (dimer_matsubara_exact(U, h, beta, taus) - dimer_matsubara_exact(U, 0.0, beta, taus)) / h ** 2
     k = slice(1, None)                     # tau = 0 is an equal-time point (its ordering differs)
     scale = np.abs(exact[k]).max()
     assert np.abs(sc[k] - exact[k]).max() < 0.02 * scale
@@ -249,7 +205,7 @@ def test_real_time_second_order_term_is_that_of_exact_diagonalisation():
     sc = sum(wb * c for wb, c in zip(w, c2_sc))
     hi = sum(wb * c for wb, c in zip(w, c2_hi))
     ts = np.arange(Nt0) * dt0
-    exact = (_dimer_greater_exact(U, h, beta, ts) - _dimer_greater_exact(U, 0.0, beta, ts)) / h ** 2
+    exact = (dimer_greater_exact(U, h, beta, ts) - dimer_greater_exact(U, 0.0, beta, ts)) / h ** 2
     k = slice(1, None)                     # t = 0 is the equal-time point
     scale = np.abs(exact[k]).max()
     assert np.abs(sc[k] - exact[k]).max() < 0.02 * scale
@@ -332,8 +288,8 @@ def test_double_occupancy_second_order_term_is_that_of_exact_diagonalisation():
     hi = sum(wb * c for wb, c in zip(w, c2_hi))
 
     def exact_docc(J):
-        _, _, rho, _ = _dimer_spectrum(U, J, beta)
-        c1u, c1d, _, _ = _dimer_fock()
+        _, _, rho, _ = dimer_spectrum(U, J, beta)
+        c1u, c1d, _, _ = dimer_fock()
         return np.trace(rho @ (c1u.T @ c1u) @ (c1d.T @ c1d))
 
     exact = (exact_docc(h) - exact_docc(0.0)) / h ** 2
