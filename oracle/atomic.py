@@ -31,7 +31,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .contour import Contour, FWD, BWD, IMAG
+from .contour import Contour, BWD, IMAG
 
 
 def boltzmann_log_weights(eps0: float, U0: float, beta: float):

@@ -12,7 +12,6 @@ gradient through torch's chain rule.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import binding
