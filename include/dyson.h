@@ -208,7 +208,8 @@ int dyson_observables(dyson_ctx* ctx, double* n, double* ekin, double* docc, int
  * gloc[s][z][z'] = G_ss(z, z'), DEVICE memory [Nr][Nc][Nc] complex128 (rows of
  * sites not in src are left untouched).  With DYSON_SYMMETRY_C4V one site per
  * orbit is solved and every other requested site receives its representative's
- * block (G_{g(r), g(r)} = G_{r, r}, App. A); this holds while the installed local
+ * block (G_{g(r), g(r)} = G_{r, r}, App. A; the representative's own row is
+ * written too, requested or not); this holds while the installed local
  * blocks are C4v-invariant too, as they stay when every self-energy step is fed
  * local Green's functions of this kind.  The input of the self-energy step below. */
 int dyson_local_greens(dyson_ctx* ctx, const int32_t* src_sites, int64_t n_src, int precision, double tol,
