@@ -55,7 +55,8 @@ def parse():
                     help="instances of the seeded uneven batch in the batched-solve leg (0 skips it)")
     ap.add_argument("--no-driven", action="store_true", help="skip the driven 32x32 (Nc = 384) leg")
     ap.add_argument("--no-selfenergy", action="store_true", help="skip the self-consistency loop leg")
-    ap.add_argument("--sweep-variant", default="auto", choices=["auto", "single_cta", "cta_pair"],
+    ap.add_argument("--sweep-variant", default="auto",
+                    choices=["auto", "single_cta", "cta_pair", "fused_pair", "fused_pair_wide"],
                     help="override the autotuner's sweep variant (profiling runs: kernel timings under a "
                          "profiler can flip the tuner's choice)")
     ap.add_argument("--lattice", type=int, default=16,
@@ -423,7 +424,7 @@ def run_gb300(args, rank, world, local):
     solver.build_sigma()
     tuning = solver.autotune(args.batch)
     if args.sweep_variant != "auto":
-        tuning["sweep_variant"] = ["single_cta", "cta_pair"].index(args.sweep_variant)
+        tuning["sweep_variant"] = binding.SWEEP_NAMES.index(args.sweep_variant)
         solver.set_sweep_variant(tuning["sweep_variant"])
     for k in range(args.warmup):
         step(k)
@@ -597,10 +598,10 @@ def run_gb300(args, rank, world, local):
             "contour_gemm_tflops": tflops_local * world,
             "vector_columns_per_s": value * Nc,
             "sweeps_per_step": sweeps, "refinements_per_step": refinements, "max_rel_residual": residual,
-            "autotune": {"sweep_variant": ["single_cta", "cta_pair"][tuning["sweep_variant"]],
+            "autotune": {"sweep_variant": binding.SWEEP_NAMES[tuning["sweep_variant"]],
                          "variant_pinned": args.sweep_variant != "auto",
                          "chunk_block_columns": tuning["chunk_block_columns"],
-                         "candidates": [(["single_cta", "cta_pair"][c["variant"]], c["chunk"],
+                         "candidates": [(binding.SWEEP_NAMES[c["variant"]], c["chunk"],
                                          round(c["vector_columns_per_s"])) for c in tuning["candidates"]]},
             "roofline": roof, "rooflines": rooflines, "kernels": kernels, "clocks": clk,
             "gpu_launches": gpu_launches}

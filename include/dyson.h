@@ -295,7 +295,8 @@ enum {
   DYSON_KERNEL_SWEEP_TC_PAIR = 5, /* the same GEMM on CTA pairs (tcgen05 cta_group::2, M=256) */
   DYSON_KERNEL_GATHER_TC = 6,     /* neighbour gather X = J d of the tensor-core sweep        */
   DYSON_KERNEL_SELFENERGY = 7,    /* connected cumulant contraction of the self-energy step  */
-  DYSON_KERNEL_KINDS = 8
+  DYSON_KERNEL_SWEEP_TC_FUSED = 8,/* fused gather + 3xTF32 GEMM on CTA pairs (one launch/sweep)*/
+  DYSON_KERNEL_KINDS = 9
 };
 
 /* Enable (1) or disable (0) event timing of every sweep/residual launch on the
@@ -312,14 +313,29 @@ int64_t dyson_launch_count(const dyson_ctx* ctx);
 /* Cap the number of block columns solved together (0 = size from free memory). */
 int dyson_set_chunk(dyson_ctx* ctx, int32_t block_columns);
 
-/* Form of the 3xTF32 tensor-core sweep.  SINGLE_CTA: one CTA per 128 x 256
- * output tile (the default).  CTA_PAIR: clusters of two CTAs on 256 x 256 tiles
- * with tcgen05 cta_group::2 MMAs; used only when Nc is a multiple of 128 and
- * the device can co-schedule CTA pairs, otherwise the single-CTA form runs.
- * Both give the same results to FP32 rounding; which is faster depends on the
+/* Form of the 3xTF32 tensor-core sweep (App. C's series step; Sec. IV.D's
+ * blocked application of the local blocks to many right-hand sides).
+ *   SINGLE_CTA  a gather launch writes X = J d to global memory, then one CTA
+ *               per 128 x 256 output tile multiplies (the default);
+ *   CTA_PAIR    the same gather, then clusters of two CTAs on 256 x 256 tiles
+ *               with tcgen05 cta_group::2 MMAs;
+ *   FUSED_PAIR  one launch per sweep: CTA pairs whose producer warps gather the
+ *               four neighbour rows of d straight into the MMA's shared-memory
+ *               operand (X never reaches global memory); tiles of 256 rows x 256
+ *               columns, two TMEM accumulators;
+ *   FUSED_PAIR_WIDE  the fused form with tiles of 512 rows x 256 columns (X
+ *               gathered once per site and column tile, one accumulator set).
+ * The pair forms need Nc % 128 == 0 (FUSED_PAIR_WIDE: Nc % 256 == 0) and a
+ * device that co-schedules CTA pairs; otherwise the single-CTA form runs.  All
+ * give the same results to FP32 rounding; which is fastest depends on the
  * shape, which is what dyson_autotune measures.  Returns INVALID_ARG for an
  * unknown variant. */
-enum { DYSON_SWEEP_SINGLE_CTA = 0, DYSON_SWEEP_CTA_PAIR = 1 };
+enum {
+  DYSON_SWEEP_SINGLE_CTA = 0,
+  DYSON_SWEEP_CTA_PAIR = 1,
+  DYSON_SWEEP_FUSED_PAIR = 2,
+  DYSON_SWEEP_FUSED_PAIR_WIDE = 3
+};
 int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
 
 /* Point-group symmetry of the problem (App. A).  DYSON_SYMMETRY_C4V: on a
@@ -339,11 +355,12 @@ int dyson_set_symmetry(dyson_ctx* ctx, int mode);
 
 /* Autotuner of the tensor-core sweep.  On this context's Lambda it times two
  * warm-up and three timed sweeps for each candidate: every sweep variant the
- * contour allows (DYSON_SWEEP_SINGLE_CTA; DYSON_SWEEP_CTA_PAIR where Nc is a
- * multiple of 128) times every chunk of 1, 2, 4, ... block columns up to
+ * contour allows (DYSON_SWEEP_SINGLE_CTA; DYSON_SWEEP_CTA_PAIR and
+ * DYSON_SWEEP_FUSED_PAIR where Nc is a multiple of 128; DYSON_SWEEP_FUSED_PAIR_WIDE
+ * where it is a multiple of 256) times every chunk of 1, 2, 4, ... block columns up to
  * max_block_columns and to what fits in 85 % of free device memory.  Then it
  * sets the context to the fastest (dyson_set_sweep_variant and dyson_set_chunk;
- * candidates are tried largest chunk first, single CTA before pair, and a later
+ * candidates are tried largest chunk first, in the variant order above, and a later
  * one wins only when it is more than 2 % faster, so that timing noise does not
  * flip the choice) and, when out is not NULL, reports the choice and every candidate's measured
  * sweep throughput in vector columns per second.  Needs a built, upright Lambda
@@ -458,11 +475,18 @@ void dyson_batch_destroy(dyson_batch* b);
  * INVALID_ARG (see dyson_noalloc_last_error).  Returns OK, NOT_CONVERGED
  * (g_out holds the last iterate), DIVERGED, INVALID_ARG or CUDA.
  *
- * The first call on each device looks up the device address of the scratch
- * array (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture.  All calls share the one array and it keeps the
- * previous call's contents (the call clears what must start at zero): calls
- * that overlap on the GPU, from several threads or streams, race on it. */
+ * With CUDA's lazy module loading the array is committed on a device when the
+ * module that holds it is first loaded there: by dyson_init on that device, or
+ * else by the first call of this function on it, which also looks up the
+ * array's device address (cudaGetSymbolAddress with that device current).  A
+ * caller whose heap another framework will take must therefore create a
+ * context, or make one call, on each device before that happens.  The call
+ * synchronises: it copies each sweep's norm to the host and waits for it, so
+ * it blocks the host until the solve is done and cannot be called while its
+ * stream is being captured into a CUDA graph.  All calls share the one array
+ * and it keeps the previous call's contents (the call clears what must start
+ * at zero): calls that overlap on the GPU, from several threads or streams,
+ * race on it. */
 #define DYSON_NOALLOC_MAX_STATE_BYTES (16u << 20)
 
 int dyson_solve_block_column_noalloc(const double* lambda, const double* J, int32_t Lx, int32_t Ly, int32_t Nt,

@@ -21,9 +21,10 @@ ERR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "OOM", -3: "NOT_CONVERGED", -4: "DI
 PREC_F64 = 0
 PREC_TF32X3_F64REF = 1
 KERNEL_SWEEP_F64, KERNEL_SWEEP_F32, KERNEL_SWEEP_TC, KERNEL_RESIDUAL_F64, KERNEL_RESIDUAL_SPLIT = 0, 1, 2, 3, 4
-KERNEL_SWEEP_TC_PAIR, KERNEL_GATHER_TC = 5, 6
+KERNEL_SWEEP_TC_PAIR, KERNEL_GATHER_TC, KERNEL_SELFENERGY, KERNEL_SWEEP_TC_FUSED = 5, 6, 7, 8
 KERNEL_NAMES = {0: "sweep_f64", 1: "sweep_f32_simt", 2: "sweep_tc_3xtf32", 3: "residual_f64",
-                4: "residual_split_bf16", 5: "sweep_tc_3xtf32_pair", 6: "gather_tc", 7: "selfenergy_conn"}
+                4: "residual_split_bf16", 5: "sweep_tc_3xtf32_pair", 6: "gather_tc", 7: "selfenergy_conn",
+                8: "sweep_tc_fused"}
 
 
 class Lattice(C.Structure):
@@ -77,7 +78,8 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_selfenergy_step", "dyson_selfenergy_set_anderson"]
 SYMMETRY_NONE, SYMMETRY_C4V = 0, 1
 INNER_SERIES, INNER_GMRES, INNER_AUTO = 0, 1, 2
-SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR = 0, 1
+SWEEP_SINGLE_CTA, SWEEP_CTA_PAIR, SWEEP_FUSED_PAIR, SWEEP_FUSED_PAIR_WIDE = 0, 1, 2, 3
+SWEEP_NAMES = ["single_cta", "cta_pair", "fused_pair", "fused_pair_wide"]
 
 
 def load(path: str = _LIB_PATH):

@@ -163,6 +163,23 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
   return status;
 }
 
+// one 3xTF32 tensor-core sweep dout = r + K din with per-kind event timing: the
+// fused gather + GEMM launch, or the gather launch and the GEMM launch
+int tc_timed_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, const int* act,
+                   int sweep) {
+  if (tc_uses_fused(c)) {
+    KernelTimer t(c, DYSON_KERNEL_SWEEP_TC_FUSED);
+    return tc_sweep(c, ncol, gs, r, din, dout, TC_GATHER | TC_GEMM, act, sweep);
+  }
+  int rc;
+  {
+    KernelTimer t(c, DYSON_KERNEL_GATHER_TC);
+    if ((rc = tc_sweep(c, ncol, gs, r, din, dout, TC_GATHER, act, sweep))) return rc;
+  }
+  KernelTimer t(c, tc_uses_pair(c) && !act ? DYSON_KERNEL_SWEEP_TC_PAIR : DYSON_KERNEL_SWEEP_TC);
+  return tc_sweep(c, ncol, gs, r, din, dout, TC_GEMM, act, sweep);
+}
+
 // inner solve d <- r + K d in FP32 (SIMT or 3xTF32 tensor cores)
 // act (optional): support truncation of the tensor-core sweeps (tc_sweep), valid
 // while every column of r32 is zero off its source site
@@ -173,19 +190,26 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
   if (exhausted) *exhausted = false;
   const int ng = ncol / gs;
   const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
+  // Increment form on the fused tensor-core sweep: t <- K t from t = r and the partial
+  // sum da <- da + t from da = r (the same partial sums as d <- r + K d; the update is t
+  // itself).  t alternates between db and the FP32 state after it, which the work buffer
+  // holds for the tensor-core path (48 bytes per element), while r32 stays intact.
+  const bool inc = precision == DYSON_PREC_TF32X3_F64REF && c->use_tc && tc_uses_fused(c);
+  float* t_next = db;
+  const float* t_cur = r32;
   DY_CUDA(c, cudaMemcpyAsync(da, r32, n32 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-  if (act) DY_CUDA(c, cudaMemsetAsync(db, 0, n32 * sizeof(float), c->stream));   // skipped tiles stay 0
+  if (act) DY_CUDA(c, cudaMemsetAsync(db, 0, (inc ? 2 : 1) * n32 * sizeof(float), c->stream));   // skipped tiles stay 0
   double best = std::numeric_limits<double>::infinity(), peak = 0.0;
   int since_best = 0, rc;
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
-    if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
-      {
-        KernelTimer t(c, DYSON_KERNEL_GATHER_TC);
-        if ((rc = tc_sweep(c, ncol, gs, r32, da, db, TC_GATHER, act, sweep))) return rc;
-      }
-      KernelTimer t(c, tc_uses_pair(c) && !act ? DYSON_KERNEL_SWEEP_TC_PAIR : DYSON_KERNEL_SWEEP_TC);
-      if ((rc = tc_sweep(c, ncol, gs, r32, da, db, TC_GEMM, act, sweep))) return rc;
+    if (inc) {
+      KernelTimer t(c, DYSON_KERNEL_SWEEP_TC_FUSED);
+      if ((rc = tc_sweep_inc(c, ncol, gs, t_cur, t_next, da, act, sweep))) return rc;
+      t_cur = t_next;
+      t_next = t_next == db ? db + n32 : db;
+    } else if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
+      if ((rc = tc_timed_sweep(c, ncol, gs, r32, da, db, act, sweep))) return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
       launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, ncol, gs,
@@ -195,7 +219,7 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
     DY_CUDA(c, cudaGetLastError());
     if ((rc = read_norms(c, ng, false))) return rc;
     if (c->use_tc && (rc = tc_check_error(c))) return rc;
-    std::swap(da, db);
+    if (!inc) std::swap(da, db);
     double upd = rel_max(c->h_norm, rref.data(), ng);
     rep->sweeps += 1;
     rep->gemm_flops += sweep_flops(c, ncol);
@@ -230,12 +254,7 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
 int matvec_f32(dyson_ctx* c, int ncol, int gs, int precision, const float* zero, const float* in, float* out) {
   int rc;
   if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
-    {
-      KernelTimer t(c, DYSON_KERNEL_GATHER_TC);
-      if ((rc = tc_sweep(c, ncol, gs, zero, in, out, TC_GATHER))) return rc;
-    }
-    KernelTimer t(c, tc_uses_pair(c) ? DYSON_KERNEL_SWEEP_TC_PAIR : DYSON_KERNEL_SWEEP_TC);
-    if ((rc = tc_sweep(c, ncol, gs, zero, in, out, TC_GEMM))) return rc;
+    if ((rc = tc_timed_sweep(c, ncol, gs, zero, in, out, nullptr, 0))) return rc;
   } else {
     KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
     launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, zero, in, out, c->Nr, c->Nc, ncol, gs,
@@ -430,6 +449,9 @@ int dyson_init(dyson_ctx** out, const dyson_lattice* L, const dyson_contour* C, 
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
     return fail_noctx(DYSON_ERR_INVALID_ARG, "no such CUDA device");
   DeviceGuard g(device);
+  // commit the allocation-free entry point's static scratch on this device now, not at
+  // its first call (lazy module loading); optional, so a failure only clears the error
+  if (noalloc_reserve_scratch(device) != DYSON_OK) cudaGetLastError();
   auto* c = new dyson_ctx;
   c->device = device;
   c->stream = (cudaStream_t)stream;
@@ -929,7 +951,7 @@ int dyson_set_support_truncation(dyson_ctx* c, int enable) {
 
 int dyson_set_sweep_variant(dyson_ctx* c, int variant) {
   if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
-  if (variant != DYSON_SWEEP_SINGLE_CTA && variant != DYSON_SWEEP_CTA_PAIR)
+  if (variant < DYSON_SWEEP_SINGLE_CTA || variant > DYSON_SWEEP_FUSED_PAIR_WIDE)
     return ctx_fail(c, DYSON_ERR_INVALID_ARG, "unknown sweep variant");
   c->tc_variant = variant;
   return DYSON_OK;

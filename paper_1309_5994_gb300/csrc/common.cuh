@@ -13,6 +13,16 @@
 // device helpers
 // ---------------------------------------------------------------------------
 
+// Contour conventions (Sec. IV.A; the index order of the discretised contour):
+// points 0..Nt-1 forward at t_k = k dt, Nt..2Nt-1 backward at t_{2Nt-1-z},
+// 2Nt..Nc-1 imaginary (physical time 0); quadrature weights +dt, -dt, -i beta/Nm.
+__device__ __forceinline__ int contour_time_index(int z, int Nt) {
+  return z < Nt ? z : (z < 2 * Nt ? 2 * Nt - 1 - z : 0);
+}
+__device__ __forceinline__ double2 contour_weight(int z, int Nt, int Nm, double dt, double beta) {
+  return z < Nt ? make_double2(dt, 0.0) : (z < 2 * Nt ? make_double2(-dt, 0.0) : make_double2(0.0, -beta / Nm));
+}
+
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -160,6 +170,9 @@ struct dyson_ctx {
 };
 
 int ctx_fail(dyson_ctx* c, int code, const std::string& msg);
+// load the allocation-free entry point's module on `device` (current) and look up its
+// scratch array, so the array is committed at context creation (noalloc.cu)
+int noalloc_reserve_scratch(int device);
 
 // Adjoint of L = sum_i Re(beta_i . c_i) with beta'_i = i beta_i: per site i the
 // coefficient of the row at (i, kf) (b0), at (i, kf - 1) (b1) and at (j, kf) for

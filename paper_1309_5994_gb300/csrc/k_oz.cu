@@ -74,9 +74,9 @@ struct OzState {
   bool smem_set = false;
 };
 
-__device__ __forceinline__ int time_of(int z, int Nt) { return z < Nt ? z : (z < 2 * Nt ? 2 * Nt - 1 - z : 0); }
+__device__ __forceinline__ int time_of(int z, int Nt) { return contour_time_index(z, Nt); }
 __device__ __forceinline__ double2 weight_of(int z, int Nt, int Nm, double dt, double beta) {
-  return z < Nt ? make_double2(dt, 0.0) : (z < 2 * Nt ? make_double2(-dt, 0.0) : make_double2(0.0, -beta / Nm));
+  return contour_weight(z, Nt, Nm, dt, beta);
 }
 
 // power of two >= max |v| (1 for an all-zero vector)

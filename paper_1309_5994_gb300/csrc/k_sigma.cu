@@ -6,13 +6,10 @@ namespace {
 
 // contour point z -> branch (0 forward, 1 backward, 2 imaginary) and grid index
 __device__ __forceinline__ int branch_of(int z, int Nt) { return z < Nt ? 0 : (z < 2 * Nt ? 1 : 2); }
-__device__ __forceinline__ int time_of(int z, int Nt) {
-  return z < Nt ? z : (z < 2 * Nt ? 2 * Nt - 1 - z : 0);
-}
+__device__ __forceinline__ int time_of(int z, int Nt) { return contour_time_index(z, Nt); }
 // quadrature weight of the contour measure: +dt, -dt, -i*beta/Nm
 __device__ __forceinline__ double2 weight_of(int z, int Nt, int Nm, double dt, double beta) {
-  int b = branch_of(z, Nt);
-  return b == 0 ? make_double2(dt, 0.0) : (b == 1 ? make_double2(-dt, 0.0) : make_double2(0.0, -beta / Nm));
+  return contour_weight(z, Nt, Nm, dt, beta);
 }
 
 // One thread per site: eps_i (Eq. onsitelevels), log Boltzmann weights of

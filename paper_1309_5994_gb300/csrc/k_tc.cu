@@ -69,6 +69,8 @@ struct TcState {
   int xh_ncol = -1;
   const float* xh_ptr = nullptr;
   int pair_clusters = -1;
+  // fused gather + GEMM (k_tc_fused<GT>): co-resident clusters per GT (-1: not yet asked)
+  int fused_clusters[2] = {-1, -1};
   // one-entry instance table of the single-context sweep (pinned host copy and device copy)
   TcInst* h_inst = nullptr;
   TcInst* d_inst = nullptr;
@@ -257,6 +259,51 @@ __device__ __forceinline__ void epilogue_rows(uint32_t tacc, int mg, int n_first
       d = (d == d) ? d : __int_as_float(0x7f800000);
       __stcs(dout + base + (size_t)j * N2, y);
       runmax = fmaxf(runmax, d);
+    }
+  }
+  float m = runmax;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) atomicMax(norm + qcur, nonneg_bits(m));
+}
+
+// epilogue of the increment form of the series (one warp's 32 accumulator lanes x BN
+// columns): the accumulator holds t' = K t at planar row mg, columns n_first..;
+// store t', add it to the running sum d in place, and fold max|t'| (the update of
+// the sum) into norm[] per group of gs columns
+__device__ __forceinline__ void epilogue_inc_rows(uint32_t tacc, int mg, int n_first, int site, int ncol, int gs,
+                                                  size_t N2, float* __restrict__ dsum, float* __restrict__ tout,
+                                                  unsigned long long* __restrict__ norm, int lane) {
+  using namespace ptx;
+  int qcur = n_first / gs;
+  float runmax = 0.f;
+  for (int c = 0; c < BN / 32; ++c) {
+    const int n0 = n_first + c * 32;
+    if (n0 >= ncol) break;                          // uniform across the warp
+    const int q = n0 / gs;
+    if (q != qcur) {
+      float m = runmax;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0) atomicMax(norm + qcur, nonneg_bits(m));
+      qcur = q;
+      runmax = 0.f;
+    }
+    float dv[32];
+    uint32_t v[32];
+    const size_t base = ((size_t)site * ncol + n0) * N2 + mg;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) dv[j] = __ldcs(dsum + base + (size_t)j * N2);
+    tmem_ld32(tacc + (uint32_t)(c * 32), v);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const float t = __uint_as_float(v[j]);
+      float a = fabsf(t);
+      a = (a == a) ? a : __int_as_float(0x7f800000);
+      __stcs(tout + base + (size_t)j * N2, t);
+      __stcs(dsum + base + (size_t)j * N2, dv[j] + t);
+      runmax = fmaxf(runmax, a);
     }
   }
   float m = runmax;
@@ -671,6 +718,356 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Fused sweep on CTA pairs: the neighbour gather is the producer of the MMA's
+// B operand.  Eight warps per CTA read the four neighbour rows of d_in
+// (coalesced float4 loads, all sixteen of a k-block issued back to back and one
+// k-block ahead of their sums), scale them by J(k), sum, round the sum to TF32
+// hi + lo and write both straight into the 128-byte-swizzled stage, so X never
+// exists in global memory and only Lambda hi/lo travel by TMA.  Two epilogues:
+//   INC = false  d_out = r + K d_in, norm max|d_out - d_in| (the form of the
+//                unfused sweeps; GMRES matvecs use it with r = 0);
+//   INC = true   the increment form of the series: t_out = K t_in, the running
+//                sum d += t_out in place, norm max|t_out| (one load per element
+//                in the epilogue instead of two).
+// A tile is (site, 256-column tile, GT row groups of 256 rows):
+//   GT = 1  tiles also run over the 2Nc / 256 row groups (each group-tile
+//           gathers its own copy of X; the copies meet in L2); two TMEM
+//           accumulators, so a tile's epilogue overlaps the next tile's MMAs;
+//   GT = 2  one tile covers 512 rows (2Nc = 512 or a multiple): X is gathered
+//           once per (site, column tile), the A stage holds both groups, and
+//           the two accumulators fill TMEM, so the epilogue does not overlap.
+// Sites are visited in bands of two lattice rows, column by column, so that
+// a site's neighbours are read while they are still in L2.
+// Warp roles (512 threads per CTA, both CTAs of the pair):
+//   warp 0        TMA of this CTA's 128 rows of Lambda hi/lo per group (+ L2 prefetch)
+//   warp 1        (even CTA) one thread issues the cta_group::2 MMAs
+//   warp 2        one thread waits until this CTA's Lambda tiles of a stage have landed
+//                 and its producer warps have written X, then arrives once on the even
+//                 CTA's stage barrier (the only cluster-scope release per CTA and stage;
+//                 producers arrive on a CTA-local barrier and never wait for TMA)
+//   warps 4-11    gather producers: X columns 128 r .. 128 r + 127 of the tile
+//   warps 12-15   epilogue: tcgen05.ld, + r (or += into d), store, update norm
+// Every wait is bounded like those of the other tcgen05 kernels.
+// ---------------------------------------------------------------------------
+constexpr int F_THREADS = 512;
+constexpr int F_PROD_W0 = 4, F_PROD_WARPS = 8;
+constexpr int F_EPI_W0 = 12;
+constexpr int F_A_GROUP = 2 * A_TILE;                   // Lambda hi + lo, one row group, this CTA's 128 rows
+constexpr int F_SITE_BAND = 2;                          // lattice rows per band of the site order
+constexpr int F_RELAY_W = 2;                            // warp 2: relays "Lambda landed" to the even CTA
+template <int GT>
+struct FusedCfg {
+  static constexpr int STAGE = GT * F_A_GROUP + 2 * PX_TILE;
+  static constexpr int STAGES = GT == 1 ? 3 : 2;
+  static constexpr int SMEM = STAGES * STAGE + 1024;
+  static constexpr int NBUF = 2 / GT;                   // accumulator sets of GT x 256 columns
+  static_assert(NBUF * GT * BN <= 512, "TMEM holds 512 columns");
+};
+
+// site of visit index v: bands of F_SITE_BAND lattice rows, walked column by column
+__device__ __forceinline__ int band_site(int v, int Lx, int Ly) {
+  const int band = v / (F_SITE_BAND * Lx);
+  const int y0 = band * F_SITE_BAND;
+  const int h = min(F_SITE_BAND, Ly - y0);
+  const int w = v - band * F_SITE_BAND * Lx;
+  return (y0 + w % h) * Lx + w / h;
+}
+
+struct FTile {
+  int site, nt, gt;
+  bool active;
+};
+__device__ __forceinline__ FTile fused_tile(int tile, int NGT, int NT, int Lx, int Ly, const int* __restrict__ act,
+                                            int sweep) {
+  FTile T;
+  T.gt = tile % NGT;
+  T.nt = (tile / NGT) % NT;
+  T.site = band_site(tile / (NGT * NT), Lx, Ly);
+  T.active = !(act && act[T.site * NT + T.nt] > sweep);
+  return T;
+}
+
+template <int GT, bool INC>
+__global__ void __launch_bounds__(F_THREADS, 1)
+    k_tc_fused(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
+               const float* __restrict__ r, const float* __restrict__ din, float* __restrict__ dout,
+               float* __restrict__ dacc,
+               const float* __restrict__ Jz, const int* __restrict__ nbr, const int* __restrict__ nbond, int Lx,
+               int Ly, int Nc, int ncol, int gs, unsigned long long* __restrict__ norm, int* __restrict__ err,
+               const int* __restrict__ act, int sweep) {
+  using namespace ptx;
+  using Cfg = FusedCfg<GT>;
+  constexpr int STAGES = Cfg::STAGES, NBUF = Cfg::NBUF, STAGE = Cfg::STAGE;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_a[STAGES], xready[STAGES], full[STAGES], empty[STAGES];
+  __shared__ __align__(8) uint64_t acc_full[NBUF], acc_empty[NBUF], drain;
+  __shared__ uint32_t tmem_holder;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+  const int N2 = 2 * Nc, KB = N2 / BK;
+  const int NGT = N2 / (PM * GT);
+  const int NT = (ncol + BN - 1) / BN;
+  const int tiles = Lx * Ly * NT * NGT;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_a[s], 1);
+      mbar_init(&xready[s], F_PROD_WARPS);              // this CTA's producer warps wrote X
+      mbar_init(&full[s], 2);                           // each CTA's relay (even CTA's copy)
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 256);                    // 128 epilogue threads of each CTA
+    }
+    mbar_init(&drain, 1);
+    abort_flag = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc_pair(&tmem_holder, TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  tc_fence_after();
+  const uint32_t tmem = tmem_holder;
+  volatile int* abort_p = &abort_flag;
+  auto stage_ptr = [&](int s) { return smem + (size_t)s * STAGE; };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA: Lambda hi / lo (each CTA its own rows) ----------------
+      int g = 0;
+      bool ok = true;
+      for (int tile = pair; tile < tiles && ok; tile += npairs) {
+        const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
+        if (!T.active) continue;
+        int t2 = tile + npairs;
+        FTile N;
+        N.active = false;
+        for (; t2 < tiles; t2 += npairs) {
+          N = fused_tile(t2, NGT, NT, Lx, Ly, act, sweep);
+          if (N.active) break;
+        }
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1, abort_p)) {
+            ok = false;
+            break;
+          }
+          uint8_t* st = stage_ptr(s);
+          mbar_expect_tx(&full_a[s], GT * F_A_GROUP);
+#pragma unroll
+          for (int gi = 0; gi < GT; ++gi) {
+            const int row0 = (T.gt * GT + gi) * PM + (int)rank * BM;
+            tma_load_3d(st + gi * F_A_GROUP, &map_ahi, &full_a[s], kb * BK, row0, T.site);
+            tma_load_3d(st + gi * F_A_GROUP + A_TILE, &map_alo, &full_a[s], kb * BK, row0, T.site);
+          }
+          const int ahead = kb + PREFETCH;
+          const FTile* P = ahead < KB ? &T : (N.active && ahead - KB < KB ? &N : nullptr);
+          if (P) {
+            const int k2 = ahead < KB ? ahead : ahead - KB;
+#pragma unroll
+            for (int gi = 0; gi < GT; ++gi) {
+              const int row0 = (P->gt * GT + gi) * PM + (int)rank * BM;
+              tma_prefetch_3d(&map_ahi, k2 * BK, row0, P->site);
+              tma_prefetch_3d(&map_alo, k2 * BK, row0, P->site);
+            }
+          }
+        }
+      }
+      for (int q = g > STAGES ? g - STAGES : 0; q < g; ++q)
+        mbar_wait(&full_a[q % STAGES], (q / STAGES) & 1, abort_p, false);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 0) {
+      // ---------------- MMA issuer (even CTA) ----------------
+      int g = 0, t = 0;
+      bool ok = true, any = false;
+      for (int tile = pair; tile < tiles && ok; tile += npairs) {
+        const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
+        if (!T.active) continue;
+        const int buf = t % NBUF;
+        if (t >= NBUF && !mbar_wait_cluster(&acc_empty[buf], ((t / NBUF) - 1) & 1, abort_p)) break;
+        ++t;
+        tc_fence_after();
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (!mbar_wait_cluster(&full[s], (g / STAGES) & 1, abort_p)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(stage_ptr(s));
+          const uint32_t x_hi = st + GT * F_A_GROUP, x_lo = x_hi + PX_TILE;
+#pragma unroll
+          for (int k8 = 0; k8 < BK / 8; ++k8) {
+            const uint32_t off = k8 * 32;
+            const uint64_t dxh = sdesc_sw128(x_hi + off), dxl = sdesc_sw128(x_lo + off);
+#pragma unroll
+            for (int gi = 0; gi < GT; ++gi) {
+              const uint32_t a_hi = st + gi * F_A_GROUP, a_lo = a_hi + A_TILE;
+              const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
+              const uint32_t dacc = tmem + (uint32_t)((buf * GT + gi) * BN);
+              mma_pair_tf32(dacc, dah, dxh, P_IDESC, (kb | k8) ? 1u : 0u);
+              mma_pair_tf32(dacc, dah, dxl, P_IDESC, 1u);
+              mma_pair_tf32(dacc, dal, dxh, P_IDESC, 1u);
+            }
+          }
+          mma_commit_pair_mc(&empty[s], 0x3);
+          any = true;
+        }
+        if (ok) mma_commit_pair_mc(&acc_full[buf], 0x3);
+      }
+      if (any) {
+        mma_commit_pair_mc(&drain, 0x1);
+        mbar_wait(&drain, 0, abort_p, false);
+      }
+    }
+  } else if (warp >= F_PROD_W0 && warp < F_PROD_W0 + F_PROD_WARPS) {
+    // ---------------- gather producers (both CTAs) ----------------
+    // thread pt: 16-byte chunk j of the k-block row (k = 32 kb + 4 j .. + 3) for the
+    // tile columns c0 + 32 i, i = 0..3, of this CTA's half
+    const int pt = threadIdx.x - F_PROD_W0 * 32;
+    const int j = pt & 7, c0 = pt >> 3;
+    int g = 0;
+    int ok = 1;
+    for (int tile = pair; tile < tiles && ok; tile += npairs) {
+      const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
+      if (!T.active) continue;
+      int nb[4], bd[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        nb[q] = __ldg(nbr + T.site * 4 + q);
+        bd[q] = nb[q] >= 0 ? __ldg(nbond + T.site * 4 + q) : 0;
+      }
+      const int col0 = T.nt * BN + (int)rank * (BN / 2);
+      // this thread's columns col0 + c0 + 32 i, i < ni, lie before the end
+      const int ni = max(0, min(4, (ncol - col0 - c0 + 31) / 32));
+      // row of neighbour q at the first column (a valid address also where the neighbour is missing)
+      const float* nbp[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        nbp[q] = din + (nb[q] >= 0 && ni > 0 ? ((size_t)nb[q] * ncol + col0 + c0) * N2 : 0) + 4 * j;
+      const size_t cstride = (size_t)32 * N2;            // 32 columns further
+      // sixteen neighbour loads and four hopping loads per k-block, issued back to back
+      // (no load behind a branch) one k-block ahead of their sums, so that their latency
+      // overlaps the previous k-block's stage wait and shared-memory stores
+      float4 v[4][4], jv[4];
+      auto issue = [&](int kb) {
+        const int k = kb * BK + 4 * j;
+        const int kz = k < Nc ? k : k - Nc;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          jv[q] = __ldg(reinterpret_cast<const float4*>(Jz + (size_t)bd[q] * Nc + kz));
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const bool ok_qi = nb[q] >= 0 && i < ni;
+            v[q][i] = __ldg(reinterpret_cast<const float4*>(ok_qi ? nbp[q] + i * cstride + kb * BK : nbp[q]));
+          }
+        }
+      };
+      issue(0);
+      for (int kb = 0; kb < KB; ++kb, ++g) {
+        const int s = g % STAGES;
+        float4 acc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (nb[q] >= 0 && i < ni) {
+              acc[i].x = fmaf(jv[q].x, v[q][i].x, acc[i].x);
+              acc[i].y = fmaf(jv[q].y, v[q][i].y, acc[i].y);
+              acc[i].z = fmaf(jv[q].z, v[q][i].z, acc[i].z);
+              acc[i].w = fmaf(jv[q].w, v[q][i].w, acc[i].w);
+            }
+          }
+        }
+        if (kb + 1 < KB) issue(kb + 1);
+        if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1, abort_p)) ok = 0;
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) break;
+        uint8_t* xs = stage_ptr(s) + GT * F_A_GROUP;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int c = c0 + 32 * i;
+          const int off = c * 128 + ((j ^ (c & 7)) << 4);
+          float4 h, l;
+          h.x = to_tf32(acc[i].x); l.x = to_tf32(acc[i].x - h.x);
+          h.y = to_tf32(acc[i].y); l.y = to_tf32(acc[i].y - h.y);
+          h.z = to_tf32(acc[i].z); l.z = to_tf32(acc[i].z - h.z);
+          h.w = to_tf32(acc[i].w); l.w = to_tf32(acc[i].w - h.w);
+          *reinterpret_cast<float4*>(xs + off) = h;
+          *reinterpret_cast<float4*>(xs + PX_TILE + off) = l;
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&xready[s]);
+      }
+    }
+  } else if (warp == F_RELAY_W) {
+    if (lane == 0) {
+      // ---------------- relay: this CTA's stage complete -> even CTA's stage barrier ----------------
+      const uint32_t full_bar0 = mapa(smem_u32(&full[0]), 0);
+      int g = 0;
+      bool ok = true;
+      for (int tile = pair; tile < tiles && ok; tile += npairs) {
+        const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
+        if (!T.active) continue;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % STAGES;
+          if (!mbar_wait(&full_a[s], (g / STAGES) & 1, abort_p) || !mbar_wait(&xready[s], (g / STAGES) & 1, abort_p)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_remote(full_bar0 + (uint32_t)(s * 8));
+        }
+      }
+    }
+  } else if (warp >= F_EPI_W0) {
+    // ---------------- epilogue (both CTAs, own 128 rows of each group) ----------------
+    const int q4 = warp - F_EPI_W0;
+    const uint32_t empty_bar0 = mapa(smem_u32(&acc_empty[0]), 0);
+    int t = 0;
+    for (int tile = pair; tile < tiles; tile += npairs) {
+      const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
+      if (!T.active) continue;
+      const int buf = t % NBUF;
+      bool go = mbar_wait(&acc_full[buf], (t / NBUF) & 1, abort_p);
+      ++t;
+      go = __all_sync(0xffffffffu, go);
+      if (!go) break;
+      tc_fence_after();
+#pragma unroll
+      for (int gi = 0; gi < GT; ++gi) {
+        const uint32_t tacc = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((buf * GT + gi) * BN);
+        const int mg = (T.gt * GT + gi) * PM + (int)rank * BM + q4 * 32 + lane;
+        if (INC)
+          epilogue_inc_rows(tacc, mg, T.nt * BN, T.site, ncol, gs, (size_t)N2, dacc, dout, norm, lane);
+        else
+          epilogue_rows(tacc, mg, T.nt * BN, T.site, ncol, gs, (size_t)N2, r, din, dout, norm, lane);
+      }
+      tc_fence_before();
+      mbar_arrive_remote(empty_bar0 + (uint32_t)(buf * sizeof(uint64_t)));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc_pair(tmem, TMEM_COLS);
+  }
+  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -730,7 +1127,50 @@ int pair_clusters(dyson_ctx* c, TcState* st) {
   return st->pair_clusters;
 }
 
+// co-resident CTA pairs of k_tc_fused<GT> on this device (0: it cannot run)
+template <int GT>
+int fused_clusters(dyson_ctx* c, TcState* st) {
+  int& n = st->fused_clusters[GT - 1];
+  if (n >= 0) return n;
+  n = 0;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) sms = 0;
+  if (sms >= 2 &&
+      cudaFuncSetAttribute(k_tc_fused<GT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           FusedCfg<GT>::SMEM) == cudaSuccess &&
+      cudaFuncSetAttribute(k_tc_fused<GT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           FusedCfg<GT>::SMEM) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (unsigned)(sms / 2));
+    cfg.blockDim = dim3(F_THREADS);
+    cfg.dynamicSmemBytes = FusedCfg<GT>::SMEM;
+    cfg.stream = c->stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_tc_fused<GT, false>, &cfg) == cudaSuccess) n = ncl;
+  }
+  cudaGetLastError();
+  return n;
+}
+
+// row groups per fused tile for the context's variant (0: the fused kernel does not serve it)
+int fused_gt(dyson_ctx* c) {
+  if (c->Nc % 128 != 0 || c->Lx * c->Ly != c->Nr) return 0;
+  if (c->tc_variant == DYSON_SWEEP_FUSED_PAIR) return fused_clusters<1>(c, state(c)) > 0 ? 1 : 0;
+  if (c->tc_variant == DYSON_SWEEP_FUSED_PAIR_WIDE && c->Nc % 256 == 0)
+    return fused_clusters<2>(c, state(c)) > 0 ? 2 : 0;
+  return 0;
+}
+
 }  // namespace
+
+bool tc_uses_fused(dyson_ctx* c) { return fused_gt(c) > 0; }
 
 bool tc_uses_pair(dyson_ctx* c) {
   return c->tc_variant == DYSON_SWEEP_CTA_PAIR && c->Nc % 128 == 0 && pair_clusters(c, state(c)) > 0;
@@ -744,7 +1184,7 @@ bool tc_supported(dyson_ctx* c, int Nc) {
 namespace {
 
 // tensor maps of Lambda and the gather buffer of context c for ncol columns
-int tc_prepare(dyson_ctx* c, int ncol) {
+int tc_prepare(dyson_ctx* c, int ncol, bool need_x = true) {
   TcState* st = state(c);
   const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;
   if (!st->d_err) {
@@ -761,6 +1201,13 @@ int tc_prepare(dyson_ctx* c, int ncol) {
     st->a_Nc = Nc;
     st->inst_valid = false;
   }
+  if (!st->smem_set) {
+    DY_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    DY_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<TC_MAX_INSTANCES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    SMEM_BYTES));
+    st->smem_set = true;
+  }
+  if (!need_x) return DYSON_OK;                          // the fused sweep gathers in shared memory
   size_t xbytes = (size_t)Nr * ncol * N2 * sizeof(float);
   if (st->xbuf_bytes < xbytes) {
     if (st->xbuf) cudaFree(st->xbuf);
@@ -781,12 +1228,33 @@ int tc_prepare(dyson_ctx* c, int ncol) {
     st->x_ncol = ncol;
     st->inst_valid = false;
   }
-  if (!st->smem_set) {
-    DY_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    DY_CUDA(c, cudaFuncSetAttribute(k_tc_gemm<TC_MAX_INSTANCES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    SMEM_BYTES));
-    st->smem_set = true;
-  }
+  return DYSON_OK;
+}
+
+template <int GT, bool INC>
+int launch_fused(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, float* dacc,
+                 const int* act, int sweep) {
+  TcState* st = state(c);
+  const long long tiles = (long long)c->Nr * ((ncol + BN - 1) / BN) * ((2 * c->Nc) / (PM * GT));
+  const int pairs = (int)std::min<long long>(tiles, fused_clusters<GT>(c, st));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * (unsigned)pairs);
+  cfg.blockDim = dim3(F_THREADS);
+  cfg.dynamicSmemBytes = FusedCfg<GT>::SMEM;
+  cfg.stream = c->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  DY_CUDA(c, cudaLaunchKernelEx(&cfg, k_tc_fused<GT, INC>, st->a_hi, st->a_lo, r, din, dout, dacc,
+                                (const float*)c->d_Jz,
+                                (const int*)c->d_nbr, (const int*)c->d_nbond, c->Lx, c->Ly, c->Nc, ncol, gs,
+                                c->d_norm, st->d_err, act, sweep));
+  DY_CUDA(c, cudaGetLastError());
+  c->launches += 1;
   return DYSON_OK;
 }
 
@@ -873,8 +1341,15 @@ int tc_launch_table(dyson_ctx* c, const TcInst* d_tab, int ninst, int tiles, int
 
 int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, int phases,
              const int* act, int sweep) {
-  int rc = tc_prepare(c, ncol);
+  const int gt = (phases & TC_TABLE_ONLY) ? 0 : fused_gt(c);
+  int rc = tc_prepare(c, ncol, gt == 0);
   if (rc) return rc;
+  if (gt > 0) {
+    // one launch gathers and multiplies: the gather phase alone launches nothing
+    if (!(phases & TC_GEMM)) return DYSON_OK;
+    return gt == 1 ? launch_fused<1, false>(c, ncol, gs, r, din, dout, nullptr, act, sweep)
+                   : launch_fused<2, false>(c, ncol, gs, r, din, dout, nullptr, act, sweep);
+  }
   TcState* st = state(c);
   const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;
   // truncated sweeps run on the single-CTA kernel, which skips tiles
@@ -934,6 +1409,16 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
   }
   return tc_launch_table(c, st->d_inst, 1, tc_instance_tiles(*h), tc_instance_gather_blocks(*h), parity,
                          phases & (TC_GATHER | TC_GEMM), c->stream, &st->a_hi, &st->a_lo, &st->x, h, act, sweep);
+}
+
+int tc_sweep_inc(dyson_ctx* c, int ncol, int gs, const float* tin, float* tout, float* dsum, const int* act,
+                 int sweep) {
+  const int gt = fused_gt(c);
+  if (gt == 0) return ctx_fail(c, DYSON_ERR_STATE, "the increment-form sweep needs a fused sweep variant");
+  int rc = tc_prepare(c, ncol, false);
+  if (rc) return rc;
+  return gt == 1 ? launch_fused<1, true>(c, ncol, gs, nullptr, tin, tout, dsum, act, sweep)
+                 : launch_fused<2, true>(c, ncol, gs, nullptr, tin, tout, dsum, act, sweep);
 }
 
 int tc_check_error(dyson_ctx* c) {

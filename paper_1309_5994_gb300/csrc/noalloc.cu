@@ -18,7 +18,10 @@
 
 namespace {
 
-// scratch: the second state buffer of the ping-pong series plus two norm words
+// scratch: the second state buffer of the ping-pong series plus two norm words.
+// With CUDA's lazy module loading the array is committed on a device when this
+// file's module is first loaded there: by dyson_init on that device, or by the
+// first dyson_solve_block_column_noalloc call, whichever comes first.
 constexpr size_t kStateBytes = (size_t)DYSON_NOALLOC_MAX_STATE_BYTES;
 constexpr size_t kWordsBytes = 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kStateBytes + kWordsBytes];
@@ -34,10 +37,6 @@ int fail(int code, const std::string& m) {
   return code;
 }
 
-__device__ __forceinline__ int time_index(int z, int Nt) { return z < Nt ? z : (z < 2 * Nt ? 2 * Nt - 1 - z : 0); }
-__device__ __forceinline__ double2 contour_weight(int z, int Nt, int Nm, double dt, double beta) {
-  return z < Nt ? make_double2(dt, 0.0) : (z < 2 * Nt ? make_double2(-dt, 0.0) : make_double2(0.0, -beta / Nm));
-}
 __device__ __forceinline__ unsigned long long nonneg(double v) {
   if (!(v >= 0.0)) v = __longlong_as_double(0x7ff0000000000000ULL);
   return (unsigned long long)__double_as_longlong(v);
@@ -95,7 +94,7 @@ __global__ __launch_bounds__(256) void k_na_sweep(const double2* __restrict__ la
       double2 v = make_double2(0.0, 0.0);
       if (kk < Nc && cc < Nc) {
         double jr = 0.0, ji = 0.0;
-        int tk = time_index(kk, Nt);
+        int tk = contour_time_index(kk, Nt);
         for (int q = 0; q < 4; ++q) {
           if (nb[q] < 0) continue;
           double Jv = J[(size_t)bd[q] * Nt + tk];
@@ -165,6 +164,13 @@ double bits_to_d(unsigned long long b) {
 }
 
 }  // namespace
+
+// dyson_init's set-up for `device` (current): loads this module and looks up the
+// scratch address, so that the array is committed when a context is created
+int noalloc_reserve_scratch(int device) {
+  void* p = nullptr;
+  return scratch_address(device, &p);
+}
 
 extern "C" const char* dyson_noalloc_last_error(void) { return g_noalloc_err.c_str(); }
 

@@ -36,6 +36,10 @@ struct TcInst {
 bool tc_supported(dyson_ctx* c, int Nc);
 // true when tc_sweep runs the CTA-pair (cta_group::2) kernel for this context
 bool tc_uses_pair(dyson_ctx* c);
+// true when tc_sweep runs the fused gather + GEMM kernel (k_tc_fused) for this context:
+// the context's variant is DYSON_SWEEP_FUSED_PAIR (Nc % 128 == 0) or
+// DYSON_SWEEP_FUSED_PAIR_WIDE (Nc % 256 == 0); TC_GATHER alone then launches nothing
+bool tc_uses_fused(dyson_ctx* c);
 // one sweep d_out = r + K d_in over the FP32 planar chunk state of ncol vector columns;
 // writes c->d_norm[q] for groups of gs columns (gs a multiple of 32, Nc a multiple of 64).
 // phases: TC_GATHER launches X = J d_in, TC_GEMM launches the tensor-core product and
@@ -47,6 +51,12 @@ enum { TC_GATHER = 1, TC_GEMM = 2, TC_TABLE_ONLY = 4 };
 constexpr int TC_TILE_COLS = 256;
 int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* d_in, float* d_out, int phases,
              const int* act = nullptr, int sweep = 0);
+// Increment form of one series sweep on the fused kernel (tc_uses_fused(c) must hold):
+// tout = K tin and dsum += tout over the FP32 planar chunk state; c->d_norm[q] = max |tout|
+// per group of gs columns (the update of the partial sum dsum).  act/sweep as for tc_sweep
+// (skipped tiles leave tout and dsum untouched, so tout must hold zeros there).
+int tc_sweep_inc(dyson_ctx* c, int ncol, int gs, const float* tin, float* tout, float* dsum,
+                 const int* act = nullptr, int sweep = 0);
 // DYSON_ERR_TIMEOUT if a bounded pipeline wait of an earlier sweep expired (clears the flag)
 int tc_check_error(dyson_ctx* c);
 // free tensor-core module state

@@ -9,7 +9,7 @@
 // only when it is more than 2 % faster.  Candidates are tried from the
 // largest chunk down, so the work buffers are allocated once.  The chunk sizes
 // are powers of two up to the caller's cap and to what fits in 85 % of free
-// device memory; the CTA-pair variant is tried where Nc is a multiple of 128.
+// device memory; the CTA-pair and fused variants are tried where Nc allows them.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -47,10 +47,21 @@ int time_sweeps(dyson_ctx* c, int nq, int warm, int timed, double* ms_per_sweep)
   cudaEvent_t e0, e1;
   DY_CUDA(c, cudaEventCreate(&e0));
   DY_CUDA(c, cudaEventCreate(&e1));
+  // the sweep the series runs: the increment form on the fused variants (t <- K t into
+  // db and the FP32 state after it, partial sum in da), else d <- r + K d
+  const bool inc = tc_uses_fused(c);
+  const float* t_cur = r32;
+  float* t_next = db;
   for (int s = 0; s < warm + timed; ++s) {
     if (s == warm) DY_CUDA(c, cudaEventRecord(e0, c->stream));
-    if ((rc = tc_sweep(c, ncol, c->Nc, r32, da, db, TC_GATHER | TC_GEMM))) break;
-    std::swap(da, db);
+    if (inc) {
+      if ((rc = tc_sweep_inc(c, ncol, c->Nc, t_cur, t_next, da))) break;
+      t_cur = t_next;
+      t_next = t_next == db ? db + 2 * n_el : db;
+    } else {
+      if ((rc = tc_sweep(c, ncol, c->Nc, r32, da, db, TC_GATHER | TC_GEMM))) break;
+      std::swap(da, db);
+    }
   }
   if (rc == DYSON_OK) {
     DY_CUDA(c, cudaEventRecord(e1, c->stream));
@@ -90,6 +101,10 @@ int dyson_autotune(dyson_ctx* c, int32_t max_block_columns, dyson_tuning* out) {
   const int saved_variant = c->tc_variant;
   c->tc_variant = DYSON_SWEEP_CTA_PAIR;
   if (tc_uses_pair(c)) variants.push_back(DYSON_SWEEP_CTA_PAIR);
+  for (int v : {DYSON_SWEEP_FUSED_PAIR, DYSON_SWEEP_FUSED_PAIR_WIDE}) {
+    c->tc_variant = v;
+    if (tc_uses_fused(c)) variants.push_back(v);
+  }
   c->tc_variant = saved_variant;
 
   dyson_tuning T;

@@ -144,17 +144,51 @@ def test_pair_kernel_ragged_column_tiles(torch_cuda, lib):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
 
-@pytest.mark.parametrize("case", ["nc64_ragged", "nc256_pair"])
+FUSED_CASES = [
+    # (problem, sources, variant): Nc = 128, three block columns (the last 256-column
+    # tile's odd half wholly past the end); Nc = 256 in both fused forms; Nc = 384
+    # (three row groups of 256) on a chain
+    (dict(L=3, Ly=2, Nt=40, Nm=48, trap_c=0.2, U0=16.0, aU=0.1, aJ=0.2, omega=20.0), [0, 3, 5], 2),
+    (dict(L=4, Ly=3, Nt=96, Nm=64, trap_c=0.1, U0=20.0, aU=0.1, aJ=0.2, omega=20.0), [0, 5, 11, 6], 2),
+    (dict(L=4, Ly=3, Nt=96, Nm=64, trap_c=0.1, U0=20.0, aU=0.1, aJ=0.2, omega=20.0), [0, 5, 11, 6], 3),
+    (dict(L=3, Ly=1, Nt=160, Nm=64, trap_c=0.1, U0=20.0), [0, 1, 2], 2),
+]
+
+
+@pytest.mark.parametrize("kw,sources,variant", FUSED_CASES)
+def test_fused_sweep_matches_dense(torch_cuda, lib, kw, sources, variant):
+    """The fused gather + GEMM sweep (one launch per sweep, X gathered into shared
+    memory) equals the dense solve, and no gather or unfused GEMM launch runs."""
+    p = wl.random_tables(wl.small(**kw), seed=17, rel=0.2)
+    S = dyson.setup(p)
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    s = _solver(p)
+    s.set_sweep_variant(variant)
+    s.profile(True)
+    got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
+    assert s.profile_query(8)[0] > 0
+    assert s.profile_query(2)[0] == s.profile_query(5)[0] == s.profile_query(6)[0] == 0
+    for q in range(len(sources)):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+    n, e, _ = s.observables()
+    for q, src in enumerate(sources):
+        n_ref, e_ref, _ = observables.observables_block_column(S, src, ref[:, :, q * p.Nc:(q + 1) * p.Nc])
+        assert np.abs(n[src] - n_ref).max() < 1e-11 and np.abs(e[src] - e_ref).max() < 1e-11
+
+
+@pytest.mark.parametrize("case", ["nc64_ragged", "nc256_pair", "nc256_fused"])
 def test_support_truncation_is_bit_identical(torch_cuda, lib, case):
     """Skipping the (site, column-tile) blocks the first series has not reached yet
     changes no bit of the result and no sweep count; both agree with the dense solve.
     Nc = 64: five block columns in two 256-column tiles (the second ragged), four
     sources sharing a tile.  Nc = 256 with the CTA-pair variant: the truncated first
-    series runs on the single-CTA kernel, the later refinements on the pair."""
+    series runs on the single-CTA kernel, the later refinements on the pair.  Nc = 256
+    with the fused variant: the fused kernel skips the tiles itself."""
     if case == "nc64_ragged":
         kw, sources, variant = dict(L=6, Ly=5, Nt=24, Nm=16, trap_c=0.1, U0=20.0), [0, 7, 29, 13, 22], 0
     else:
-        kw, sources, variant = dict(L=4, Ly=3, Nt=96, Nm=64, trap_c=0.1, U0=20.0), [0, 11], 1
+        kw, sources = dict(L=4, Ly=3, Nt=96, Nm=64, trap_c=0.1, U0=20.0), [0, 11]
+        variant = 1 if case == "nc256_pair" else 2
     p = wl.random_tables(wl.small(**kw), seed=13, rel=0.2)
     out = {}
     for trunc in (True, False):
@@ -163,13 +197,15 @@ def test_support_truncation_is_bit_identical(torch_cuda, lib, case):
         s.set_support_truncation(trunc)
         s.profile(True)
         out[trunc] = _solve(torch_cuda, s, p, sources, 1, tol=1e-13) + (
-            s.profile_query(2)[0], s.profile_query(5)[0])
+            s.profile_query(2)[0], s.profile_query(5)[0], s.profile_query(8)[0])
         s.close()
-    (g1, r1, single1, pair1), (g0, r0, single0, pair0) = out[True], out[False]
+    (g1, r1, single1, pair1, fused1), (g0, r0, single0, pair0, fused0) = out[True], out[False]
     assert np.array_equal(g1, g0)
     assert r1.report["sweeps"] == r0.report["sweeps"] and r1.report["refinements"] == r0.report["refinements"]
     if variant == 1:
         assert single1 > 0 and pair1 > 0 and single0 == 0
+    if variant == 2:
+        assert single1 == pair1 == single0 == pair0 == 0 and fused1 > 0 and fused0 > 0
     S = dyson.setup(p)
     ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
     for q in range(len(sources)):
@@ -215,7 +251,7 @@ def test_autotune_picks_a_measured_candidate_and_solves(torch_cuda, lib):
     s = _solver(p)
     t = s.autotune(6)
     cands = t["candidates"]
-    assert {c["chunk"] for c in cands} == {1, 2, 4, 6} and {c["variant"] for c in cands} == {0, 1}
+    assert {c["chunk"] for c in cands} == {1, 2, 4, 6} and {c["variant"] for c in cands} == {0, 1, 2}
     best = cands[0]                  # the documented rule: a later candidate wins only when > 2 % faster
     for c in cands[1:]:
         if c["vector_columns_per_s"] > 1.02 * best["vector_columns_per_s"]:

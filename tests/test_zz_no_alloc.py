@@ -7,7 +7,7 @@ scratch is a fixed file-scope device array.  This file is collected last so a
 failure here leaves every other test already run.  Two calls in a row, on
 different sources, must each match dyson_solve_columns (FP64) within the FP64
 path's 1e-12 relative tolerance; the second call sees the first call's leftover
-scratch contents.
+scratch contents and leaves the device's free memory unchanged.
 """
 import ctypes as C
 
@@ -42,12 +42,17 @@ def test_noalloc_matches_regular_solve_twice():
     lam_dev = torch.empty((p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda:0")
     assert lib.dyson_copy_sigma(s.h, C.c_void_p(lam_dev.data_ptr()), 1) == 0
     J_dev = torch.from_numpy(np.ascontiguousarray(p.J)).to("cuda:0")
-    for source in (5, 0):
+    for k, source in enumerate((5, 0)):
         ref = torch.empty((1, p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda:0")
         s.solve([source], precision=binding.PREC_F64, tol=1e-13, max_sweeps=400, g_out=ref)
         out = torch.full((p.Nr, p.Nc, p.Nc), float("nan"), dtype=torch.complex128, device="cuda:0")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         sweeps = _noalloc(lib, torch, p, lam_dev, J_dev, source, out)
         torch.cuda.synchronize()
+        if k == 1:
+            # the promise itself: once its kernels are loaded, a call changes no device footprint
+            assert torch.cuda.mem_get_info()[0] == free0
         assert sweeps > 1
         err = (torch.abs(out - ref[0]).max() / torch.abs(ref[0]).max()).item()
         assert err < 1e-12, f"source {source}: relative difference {err:.3e}"
