@@ -358,7 +358,9 @@ int dyson_set_symmetry(dyson_ctx* ctx, int mode);
  * contour allows (DYSON_SWEEP_SINGLE_CTA; DYSON_SWEEP_CTA_PAIR and
  * DYSON_SWEEP_FUSED_PAIR where Nc is a multiple of 128; DYSON_SWEEP_FUSED_PAIR_WIDE
  * where it is a multiple of 256) times every chunk of 1, 2, 4, ... block columns up to
- * max_block_columns and to what fits in 85 % of free device memory.  Then it
+ * max_block_columns and to what fits in 85 % of free device memory; unless the inner
+ * solver is DYSON_INNER_SERIES, also only chunks that leave room for the GMRES basis
+ * of the full restart length, so that a switch to GMRES does not restart early.  Then it
  * sets the context to the fastest (dyson_set_sweep_variant and dyson_set_chunk;
  * candidates are tried largest chunk first, in the variant order above, and a later
  * one wins only when it is more than 2 % faster, so that timing noise does not

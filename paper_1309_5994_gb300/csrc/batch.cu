@@ -41,10 +41,11 @@ struct BatchCheck {                 // what the check kernel reads per instance
 struct BatchStop {                  // inner-series stopping state per instance
   double best, peak, last;
   double target;                     // update at which this refinement's series stops
-  int since_best, sweeps, diverged, pad;
+  double hist[kStallSweeps];         // the last kStallSweeps updates (ring)
+  int since_best, sweeps, diverged, since_peak;
 };
 
-// Stopping rule of the inner series (the refinement's target, kStallDrop, kStallSweeps) per
+// Stopping rule of the inner series (the refinement's target, kStallDrop, kStallSweeps, kFlatRatio) per
 // active instance; clears the norm words for the next sweep and counts the
 // instances still active.  One block.
 __global__ void k_batch_check(const BatchCheck* __restrict__ chk, int n, int* __restrict__ active,
@@ -77,14 +78,22 @@ __global__ void k_batch_check(const BatchCheck* __restrict__ chk, int n, int* __
         S.peak = upd;
         S.best = upd;
         S.since_best = 0;
-      } else if (upd < S.best) {
-        S.best = upd;
-        S.since_best = 0;
+        S.since_peak = 0;
       } else {
-        S.since_best += 1;
+        S.since_peak += 1;
+        if (upd < S.best) {
+          S.best = upd;
+          S.since_best = 0;
+        } else {
+          S.since_best += 1;
+        }
       }
+      const double ago = S.hist[S.sweeps % kStallSweeps];
+      S.hist[S.sweeps % kStallSweeps] = upd;
       stop = (upd <= S.target && (upd < S.peak || upd == 0.0)) ||
-             (S.since_best >= kStallSweeps && S.best < kStallDrop * S.peak) || S.sweeps >= C.max_sweeps;
+             (S.since_best >= kStallSweeps && S.best < kStallDrop * S.peak) ||
+             (S.since_peak >= kStallSweeps && upd < kStallDrop * S.peak && upd > kFlatRatio * ago) ||
+             S.sweeps >= C.max_sweeps;
     }
     st[k] = S;
     if (stop) active[k] = 0;

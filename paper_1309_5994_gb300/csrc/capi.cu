@@ -190,25 +190,14 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
   if (exhausted) *exhausted = false;
   const int ng = ncol / gs;
   const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
-  // Increment form on the fused tensor-core sweep: t <- K t from t = r and the partial
-  // sum da <- da + t from da = r (the same partial sums as d <- r + K d; the update is t
-  // itself).  t alternates between db and the FP32 state after it, which the work buffer
-  // holds for the tensor-core path (48 bytes per element), while r32 stays intact.
-  const bool inc = precision == DYSON_PREC_TF32X3_F64REF && c->use_tc && tc_uses_fused(c);
-  float* t_next = db;
-  const float* t_cur = r32;
   DY_CUDA(c, cudaMemcpyAsync(da, r32, n32 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
-  if (act) DY_CUDA(c, cudaMemsetAsync(db, 0, (inc ? 2 : 1) * n32 * sizeof(float), c->stream));   // skipped tiles stay 0
+  if (act) DY_CUDA(c, cudaMemsetAsync(db, 0, n32 * sizeof(float), c->stream));   // skipped tiles stay 0
   double best = std::numeric_limits<double>::infinity(), peak = 0.0;
-  int since_best = 0, rc;
+  double hist[kStallSweeps] = {};                      // the last kStallSweeps updates (ring)
+  int since_best = 0, since_peak = 0, rc;
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
-    if (inc) {
-      KernelTimer t(c, DYSON_KERNEL_SWEEP_TC_FUSED);
-      if ((rc = tc_sweep_inc(c, ncol, gs, t_cur, t_next, da, act, sweep))) return rc;
-      t_cur = t_next;
-      t_next = t_next == db ? db + n32 : db;
-    } else if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
+    if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
       if ((rc = tc_timed_sweep(c, ncol, gs, r32, da, db, act, sweep))) return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
@@ -219,7 +208,7 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
     DY_CUDA(c, cudaGetLastError());
     if ((rc = read_norms(c, ng, false))) return rc;
     if (c->use_tc && (rc = tc_check_error(c))) return rc;
-    if (!inc) std::swap(da, db);
+    std::swap(da, db);
     double upd = rel_max(c->h_norm, rref.data(), ng);
     rep->sweeps += 1;
     rep->gemm_flops += sweep_flops(c, ncol);
@@ -231,18 +220,25 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
       peak = upd;
       best = upd;
       since_best = 0;
-    } else if (upd < best) {
-      best = upd;
-      since_best = 0;
+      since_peak = 0;
     } else {
-      ++since_best;
+      ++since_peak;
+      if (upd < best) {
+        best = upd;
+        since_best = 0;
+      } else {
+        ++since_best;
+      }
     }
+    const double ago = hist[sweep % kStallSweeps];       // the update kStallSweeps sweeps ago
+    hist[sweep % kStallSweeps] = upd;
     if (peak > abort_peak) {
       if (peak_out) *peak_out = peak;
       return DYSON_ERR_DIVERGED;                           // the caller switches to GMRES
     }
     if (upd <= target && (upd < peak || upd == 0.0)) break;   // on the decay, not before the peak
     if (since_best >= kStallSweeps && best < kStallDrop * peak) break;
+    if (since_peak >= kStallSweeps && upd < kStallDrop * peak && upd > kFlatRatio * ago) break;
     if (sweep == max_sweeps && exhausted) *exhausted = true;
   }
   *dres = da;

@@ -46,6 +46,12 @@ inline double inner_target(double floor_target, double tol, double prev_res) {
 }
 constexpr double kStallDrop = 1e-4;
 constexpr int kStallSweeps = 4;
+// The same floor seen earlier: on its FP32 floor the update fluctuates, so new minima
+// keep resetting the count above, while the decay itself has stopped.  The series also
+// stops once the update, kStallDrop below its peak, fell by less than a factor
+// kFlatRatio over the last kStallSweeps sweeps (the decay after the peak is factorial:
+// a factor 3 to 10 over four sweeps until the floor).
+constexpr double kFlatRatio = 0.8;
 
 // Refinement that grows the residual: a residual above kRefineContract times the
 // previous one, kRefineStrikes times, means the series of App. C does not

@@ -223,6 +223,9 @@ __device__ __forceinline__ void split_tile(uint8_t* x, int tt) {
 // epilogue of one warp's 32 accumulator lanes x BN columns (TMEM address tacc):
 // y = r + acc at planar row mg, columns n_first.., store y, and fold max|y - d_in|
 // into norm[] per group of gs columns (gs a multiple of 32)
+// (CH = 32 or 16 columns per tcgen05.ld; 16 keeps the register count of the 512-thread
+// fused kernel below its limit)
+template <int CH = 32>
 __device__ __forceinline__ void epilogue_rows(uint32_t tacc, int mg, int n_first, int site, int ncol, int gs,
                                               size_t N2, const float* __restrict__ r, const float* __restrict__ din,
                                               float* __restrict__ dout, unsigned long long* __restrict__ norm,
@@ -230,8 +233,8 @@ __device__ __forceinline__ void epilogue_rows(uint32_t tacc, int mg, int n_first
   using namespace ptx;
   int qcur = n_first / gs;
   float runmax = 0.f;
-  for (int c = 0; c < BN / 32; ++c) {
-    const int n0 = n_first + c * 32;
+  for (int c = 0; c < BN / CH; ++c) {
+    const int n0 = n_first + c * CH;
     if (n0 >= ncol) break;                          // uniform across the warp
     const int q = n0 / gs;
     if (q != qcur) {
@@ -242,68 +245,24 @@ __device__ __forceinline__ void epilogue_rows(uint32_t tacc, int mg, int n_first
       qcur = q;
       runmax = 0.f;
     }
-    float rv[32], dv[32];
-    uint32_t v[32];
+    float rv[CH], dv[CH];
+    uint32_t v[CH];
     const size_t base = ((size_t)site * ncol + n0) * N2 + mg;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < CH; ++j) {
       rv[j] = __ldcs(r + base + (size_t)j * N2);
       dv[j] = __ldcs(din + base + (size_t)j * N2);
     }
-    tmem_ld32(tacc + (uint32_t)(c * 32), v);
+    if (CH == 32) tmem_ld32(tacc + (uint32_t)(c * CH), v);
+    else tmem_ld16(tacc + (uint32_t)(c * CH), v);
     tmem_wait_ld();
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < CH; ++j) {
       const float y = rv[j] + __uint_as_float(v[j]);
       float d = fabsf(y - dv[j]);
       d = (d == d) ? d : __int_as_float(0x7f800000);
       __stcs(dout + base + (size_t)j * N2, y);
       runmax = fmaxf(runmax, d);
-    }
-  }
-  float m = runmax;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) atomicMax(norm + qcur, nonneg_bits(m));
-}
-
-// epilogue of the increment form of the series (one warp's 32 accumulator lanes x BN
-// columns): the accumulator holds t' = K t at planar row mg, columns n_first..;
-// store t', add it to the running sum d in place, and fold max|t'| (the update of
-// the sum) into norm[] per group of gs columns
-__device__ __forceinline__ void epilogue_inc_rows(uint32_t tacc, int mg, int n_first, int site, int ncol, int gs,
-                                                  size_t N2, float* __restrict__ dsum, float* __restrict__ tout,
-                                                  unsigned long long* __restrict__ norm, int lane) {
-  using namespace ptx;
-  int qcur = n_first / gs;
-  float runmax = 0.f;
-  for (int c = 0; c < BN / 32; ++c) {
-    const int n0 = n_first + c * 32;
-    if (n0 >= ncol) break;                          // uniform across the warp
-    const int q = n0 / gs;
-    if (q != qcur) {
-      float m = runmax;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if (lane == 0) atomicMax(norm + qcur, nonneg_bits(m));
-      qcur = q;
-      runmax = 0.f;
-    }
-    float dv[32];
-    uint32_t v[32];
-    const size_t base = ((size_t)site * ncol + n0) * N2 + mg;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) dv[j] = __ldcs(dsum + base + (size_t)j * N2);
-    tmem_ld32(tacc + (uint32_t)(c * 32), v);
-    tmem_wait_ld();
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float t = __uint_as_float(v[j]);
-      float a = fabsf(t);
-      a = (a == a) ? a : __int_as_float(0x7f800000);
-      __stcs(tout + base + (size_t)j * N2, t);
-      __stcs(dsum + base + (size_t)j * N2, dv[j] + t);
-      runmax = fmaxf(runmax, a);
     }
   }
   float m = runmax;
@@ -723,12 +682,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 // (coalesced float4 loads, all sixteen of a k-block issued back to back and one
 // k-block ahead of their sums), scale them by J(k), sum, round the sum to TF32
 // hi + lo and write both straight into the 128-byte-swizzled stage, so X never
-// exists in global memory and only Lambda hi/lo travel by TMA.  Two epilogues:
-//   INC = false  d_out = r + K d_in, norm max|d_out - d_in| (the form of the
-//                unfused sweeps; GMRES matvecs use it with r = 0);
-//   INC = true   the increment form of the series: t_out = K t_in, the running
-//                sum d += t_out in place, norm max|t_out| (one load per element
-//                in the epilogue instead of two).
+// exists in global memory and only Lambda hi/lo travel by TMA.  The epilogue
+// forms d_out = r + K d_in and the update norm max|d_out - d_in| as the unfused
+// sweeps do (GMRES matvecs use it with r = 0).
 // A tile is (site, 256-column tile, GT row groups of 256 rows):
 //   GT = 1  tiles also run over the 2Nc / 256 row groups (each group-tile
 //           gathers its own copy of X; the copies meet in L2); two TMEM
@@ -746,7 +702,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 //                 CTA's stage barrier (the only cluster-scope release per CTA and stage;
 //                 producers arrive on a CTA-local barrier and never wait for TMA)
 //   warps 4-11    gather producers: X columns 128 r .. 128 r + 127 of the tile
-//   warps 12-15   epilogue: tcgen05.ld, + r (or += into d), store, update norm
+//   warps 12-15   epilogue: tcgen05.ld, + r, store, update norm
 // Every wait is bounded like those of the other tcgen05 kernels.
 // ---------------------------------------------------------------------------
 constexpr int F_THREADS = 512;
@@ -787,11 +743,10 @@ __device__ __forceinline__ FTile fused_tile(int tile, int NGT, int NT, int Lx, i
   return T;
 }
 
-template <int GT, bool INC>
+template <int GT>
 __global__ void __launch_bounds__(F_THREADS, 1)
     k_tc_fused(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
                const float* __restrict__ r, const float* __restrict__ din, float* __restrict__ dout,
-               float* __restrict__ dacc,
                const float* __restrict__ Jz, const int* __restrict__ nbr, const int* __restrict__ nbond, int Lx,
                int Ly, int Nc, int ncol, int gs, unsigned long long* __restrict__ norm, int* __restrict__ err,
                const int* __restrict__ act, int sweep) {
@@ -1046,10 +1001,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       for (int gi = 0; gi < GT; ++gi) {
         const uint32_t tacc = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((buf * GT + gi) * BN);
         const int mg = (T.gt * GT + gi) * PM + (int)rank * BM + q4 * 32 + lane;
-        if (INC)
-          epilogue_inc_rows(tacc, mg, T.nt * BN, T.site, ncol, gs, (size_t)N2, dacc, dout, norm, lane);
-        else
-          epilogue_rows(tacc, mg, T.nt * BN, T.site, ncol, gs, (size_t)N2, r, din, dout, norm, lane);
+        epilogue_rows<16>(tacc, mg, T.nt * BN, T.site, ncol, gs, (size_t)N2, r, din, dout, norm, lane);
       }
       tc_fence_before();
       mbar_arrive_remote(empty_bar0 + (uint32_t)(buf * sizeof(uint64_t)));
@@ -1135,11 +1087,8 @@ int fused_clusters(dyson_ctx* c, TcState* st) {
   n = 0;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) sms = 0;
-  if (sms >= 2 &&
-      cudaFuncSetAttribute(k_tc_fused<GT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           FusedCfg<GT>::SMEM) == cudaSuccess &&
-      cudaFuncSetAttribute(k_tc_fused<GT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           FusedCfg<GT>::SMEM) == cudaSuccess) {
+  if (sms >= 2 && cudaFuncSetAttribute(k_tc_fused<GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       FusedCfg<GT>::SMEM) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1153,7 +1102,7 @@ int fused_clusters(dyson_ctx* c, TcState* st) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, k_tc_fused<GT, false>, &cfg) == cudaSuccess) n = ncl;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_tc_fused<GT>, &cfg) == cudaSuccess) n = ncl;
   }
   cudaGetLastError();
   return n;
@@ -1231,9 +1180,9 @@ int tc_prepare(dyson_ctx* c, int ncol, bool need_x = true) {
   return DYSON_OK;
 }
 
-template <int GT, bool INC>
-int launch_fused(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, float* dacc,
-                 const int* act, int sweep) {
+template <int GT>
+int launch_fused(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, const int* act,
+                 int sweep) {
   TcState* st = state(c);
   const long long tiles = (long long)c->Nr * ((ncol + BN - 1) / BN) * ((2 * c->Nc) / (PM * GT));
   const int pairs = (int)std::min<long long>(tiles, fused_clusters<GT>(c, st));
@@ -1249,7 +1198,7 @@ int launch_fused(dyson_ctx* c, int ncol, int gs, const float* r, const float* di
   cfg.stream = c->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  DY_CUDA(c, cudaLaunchKernelEx(&cfg, k_tc_fused<GT, INC>, st->a_hi, st->a_lo, r, din, dout, dacc,
+  DY_CUDA(c, cudaLaunchKernelEx(&cfg, k_tc_fused<GT>, st->a_hi, st->a_lo, r, din, dout,
                                 (const float*)c->d_Jz,
                                 (const int*)c->d_nbr, (const int*)c->d_nbond, c->Lx, c->Ly, c->Nc, ncol, gs,
                                 c->d_norm, st->d_err, act, sweep));
@@ -1347,8 +1296,8 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
   if (gt > 0) {
     // one launch gathers and multiplies: the gather phase alone launches nothing
     if (!(phases & TC_GEMM)) return DYSON_OK;
-    return gt == 1 ? launch_fused<1, false>(c, ncol, gs, r, din, dout, nullptr, act, sweep)
-                   : launch_fused<2, false>(c, ncol, gs, r, din, dout, nullptr, act, sweep);
+    return gt == 1 ? launch_fused<1>(c, ncol, gs, r, din, dout, act, sweep)
+                   : launch_fused<2>(c, ncol, gs, r, din, dout, act, sweep);
   }
   TcState* st = state(c);
   const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;
@@ -1409,16 +1358,6 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
   }
   return tc_launch_table(c, st->d_inst, 1, tc_instance_tiles(*h), tc_instance_gather_blocks(*h), parity,
                          phases & (TC_GATHER | TC_GEMM), c->stream, &st->a_hi, &st->a_lo, &st->x, h, act, sweep);
-}
-
-int tc_sweep_inc(dyson_ctx* c, int ncol, int gs, const float* tin, float* tout, float* dsum, const int* act,
-                 int sweep) {
-  const int gt = fused_gt(c);
-  if (gt == 0) return ctx_fail(c, DYSON_ERR_STATE, "the increment-form sweep needs a fused sweep variant");
-  int rc = tc_prepare(c, ncol, false);
-  if (rc) return rc;
-  return gt == 1 ? launch_fused<1, true>(c, ncol, gs, nullptr, tin, tout, dsum, act, sweep)
-                 : launch_fused<2, true>(c, ncol, gs, nullptr, tin, tout, dsum, act, sweep);
 }
 
 int tc_check_error(dyson_ctx* c) {

@@ -51,12 +51,6 @@ enum { TC_GATHER = 1, TC_GEMM = 2, TC_TABLE_ONLY = 4 };
 constexpr int TC_TILE_COLS = 256;
 int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* d_in, float* d_out, int phases,
              const int* act = nullptr, int sweep = 0);
-// Increment form of one series sweep on the fused kernel (tc_uses_fused(c) must hold):
-// tout = K tin and dsum += tout over the FP32 planar chunk state; c->d_norm[q] = max |tout|
-// per group of gs columns (the update of the partial sum dsum).  act/sweep as for tc_sweep
-// (skipped tiles leave tout and dsum untouched, so tout must hold zeros there).
-int tc_sweep_inc(dyson_ctx* c, int ncol, int gs, const float* tin, float* tout, float* dsum,
-                 const int* act = nullptr, int sweep = 0);
 // DYSON_ERR_TIMEOUT if a bounded pipeline wait of an earlier sweep expired (clears the flag)
 int tc_check_error(dyson_ctx* c);
 // free tensor-core module state

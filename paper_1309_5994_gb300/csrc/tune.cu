@@ -47,21 +47,10 @@ int time_sweeps(dyson_ctx* c, int nq, int warm, int timed, double* ms_per_sweep)
   cudaEvent_t e0, e1;
   DY_CUDA(c, cudaEventCreate(&e0));
   DY_CUDA(c, cudaEventCreate(&e1));
-  // the sweep the series runs: the increment form on the fused variants (t <- K t into
-  // db and the FP32 state after it, partial sum in da), else d <- r + K d
-  const bool inc = tc_uses_fused(c);
-  const float* t_cur = r32;
-  float* t_next = db;
   for (int s = 0; s < warm + timed; ++s) {
     if (s == warm) DY_CUDA(c, cudaEventRecord(e0, c->stream));
-    if (inc) {
-      if ((rc = tc_sweep_inc(c, ncol, c->Nc, t_cur, t_next, da))) break;
-      t_cur = t_next;
-      t_next = t_next == db ? db + 2 * n_el : db;
-    } else {
-      if ((rc = tc_sweep(c, ncol, c->Nc, r32, da, db, TC_GATHER | TC_GEMM))) break;
-      std::swap(da, db);
-    }
+    if ((rc = tc_sweep(c, ncol, c->Nc, r32, da, db, TC_GATHER | TC_GEMM))) break;
+    std::swap(da, db);
   }
   if (rc == DYSON_OK) {
     DY_CUDA(c, cudaEventRecord(e1, c->stream));
@@ -92,9 +81,23 @@ int dyson_autotune(dyson_ctx* c, int32_t max_block_columns, dyson_tuning* out) {
   const int64_t cap = chunk_columns(c, DYSON_PREC_TF32X3_F64REF, c->Nc, (int64_t)max_block_columns * c->Nc,
                                     &col_bytes) / c->Nc;
   if (cap < 1) return ctx_fail(c, DYSON_ERR_OOM, "one block column does not fit in device memory");
+  // a chunk whose inner solve may switch to GMRES (DYSON_INNER_AUTO or _GMRES) must leave
+  // room for the Krylov basis of the full restart length (restart + 4 FP32 states), or
+  // GMRES would restart early and converge far more slowly than the sweeps timed here
+  int64_t cap_gm = cap;
+  if (c->inner_solver != DYSON_INNER_SERIES) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+      const int m = c->gmres_restart > 0 ? c->gmres_restart : 40;
+      const double per_block = (double)c->Nc * ((double)col_bytes + (m + 4.0) * c->Nr * 2.0 * c->Nc * sizeof(float));
+      const double avail = 0.8 * (double)(free_b + c->work_bytes);
+      cap_gm = std::max<int64_t>(1, std::min<int64_t>(cap, (int64_t)(avail / per_block)));
+    }
+  }
+
   std::vector<int> chunks;
-  for (int64_t k = 1; k <= cap; k *= 2) chunks.push_back((int)k);
-  if (chunks.back() != cap) chunks.push_back((int)cap);
+  for (int64_t k = 1; k <= cap_gm; k *= 2) chunks.push_back((int)k);
+  if (chunks.back() != cap_gm) chunks.push_back((int)cap_gm);
   std::reverse(chunks.begin(), chunks.end());
   if ((rc = ensure_work(c, (size_t)chunks.front() * c->Nc * col_bytes))) return rc;
   std::vector<int> variants = {DYSON_SWEEP_SINGLE_CTA};
