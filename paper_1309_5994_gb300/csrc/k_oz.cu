@@ -21,7 +21,10 @@
 //
 // Kernels: k_oz_aprep (once per Lambda), k_oz_xprep (gather + scale + slice of X
 // per residual), k_oz_gemm (persistent: TMA + tcgen05.mma kind::f16 into two
-// accumulator sets + FP64 epilogue of the previous tile).
+// accumulator sets + FP64 epilogue of the previous tile).  With five slices the
+// accumulators of diagonals 2..6 are consecutive 48-column blocks and so are the X
+// slices in a stage: A_s X_t for t = 1..6-s is one MMA (N = (6 - s) 48) into the
+// blocks of diagonals s+1..6, five MMAs per k step for the fifteen products.
 #include <algorithm>
 
 #include <cuda_bf16.h>
@@ -335,14 +338,30 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t base = smem_u32(stage_ptr(s));
 #pragma unroll
           for (int k16 = 0; k16 < BK / 16; ++k16) {
+            if constexpr (SE + 1 == NACC + 1) {
+              // the X slices lie back to back in the stage, so A_s times X_1 .. X_{SE+1-s} is one
+              // MMA of N = (SE + 1 - s) BN whose column block t lands at accumulator s + t - 2:
+              // D starts at accumulator s - 1.  SE MMAs per k step instead of SE (SE + 1) / 2,
+              // each A slice read once from shared memory.
 #pragma unroll
-            for (int p = 0; p < SE * (SE + 1) / 2; ++p) {
-              const Prod pr = prod_of<SE>(p);
-              const uint64_t ad = sdesc_sw64(base + (pr.s - 1) * A_TILE + k16 * 32);
-              const uint64_t xd = sdesc_sw64(base + SE * A_TILE + (pr.t - 1) * X_TILE + k16 * 32);
-              // the first product of each accumulator at the first k step overwrites it
-              const bool first = (kb == 0 && k16 == 0 && (p == 0 || prod_of<SE>(p - 1).acc != pr.acc));
-              mma<0>(dacc + (uint32_t)(pr.acc * BN), ad, xd, IDESC, first ? 0u : 1u);
+              for (int sl = 1; sl <= SE; ++sl) {
+                const uint32_t n = (uint32_t)((SE + 1 - sl) * BN);
+                const uint32_t idesc = (IDESC & ~(0x3Fu << 17)) | ((n >> 3) << 17);
+                const uint64_t ad = sdesc_sw64(base + (sl - 1) * A_TILE + k16 * 32);
+                const uint64_t xd = sdesc_sw64(base + SE * A_TILE + k16 * 32);
+                // the first MMA of the tile (sl = 1 covers every accumulator) overwrites
+                mma<0>(dacc + (uint32_t)((sl - 1) * BN), ad, xd, idesc, (kb == 0 && k16 == 0 && sl == 1) ? 0u : 1u);
+              }
+            } else {
+#pragma unroll
+              for (int p = 0; p < SE * (SE + 1) / 2; ++p) {
+                const Prod pr = prod_of<SE>(p);
+                const uint64_t ad = sdesc_sw64(base + (pr.s - 1) * A_TILE + k16 * 32);
+                const uint64_t xd = sdesc_sw64(base + SE * A_TILE + (pr.t - 1) * X_TILE + k16 * 32);
+                // the first product of each accumulator at the first k step overwrites it
+                const bool first = (kb == 0 && k16 == 0 && (p == 0 || prod_of<SE>(p - 1).acc != pr.acc));
+                mma<0>(dacc + (uint32_t)(pr.acc * BN), ad, xd, IDESC, first ? 0u : 1u);
+              }
             }
           }
           mma_commit(&empty[s]);
