@@ -338,6 +338,16 @@ enum {
 };
 int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
 
+/* Time limit of the bounded waits in the tensor-core pipelines (the sweep and the
+ * split-product residual kernels), in seconds; 0 restores the default of 2 s.  The
+ * limit is held per device, so it applies to every context on ctx's device.  A wait
+ * that runs out raises the CTA's error flag; the CTA lets its in-flight copies and
+ * MMAs land (those drain waits keep the default limit), frees its tensor memory and
+ * exits, and the solve returns DYSON_ERR_TIMEOUT with the context still usable.  The
+ * paper has no counterpart: the call exists so that tests can make a healthy pipeline
+ * run out of time and check that path.  INVALID_ARG for a limit outside [0, 60]. */
+int dyson_set_wait_limit(dyson_ctx* ctx, double seconds);
+
 /* Point-group symmetry of the problem (App. A).  DYSON_SYMMETRY_C4V: on a
  * square lattice with the centred trap and drive tables invariant under the
  * eight operations of C4v (checked exactly here; INVALID_ARG otherwise),

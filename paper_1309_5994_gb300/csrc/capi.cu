@@ -206,8 +206,10 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
       c->launches += 1;
     }
     DY_CUDA(c, cudaGetLastError());
+    // one synchronisation per sweep: the norms and the pipeline's error flag come back together
+    if (c->use_tc && (rc = tc_error_enqueue(c))) return rc;
     if ((rc = read_norms(c, ng, false))) return rc;
-    if (c->use_tc && (rc = tc_check_error(c))) return rc;
+    if (c->use_tc && (rc = tc_error_status(c))) return rc;
     std::swap(da, db);
     double upd = rel_max(c->h_norm, rref.data(), ng);
     rep->sweeps += 1;
@@ -943,6 +945,16 @@ int dyson_set_support_truncation(dyson_ctx* c, int enable) {
   if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
   c->support_trunc = enable != 0;
   return DYSON_OK;
+}
+
+int dyson_set_wait_limit(dyson_ctx* c, double seconds) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (!(seconds >= 0.0) || seconds > 60.0) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "limit must be in [0, 60] s");
+  DeviceGuard g(c->device);
+  const unsigned long long ns = seconds == 0.0 ? 2000000000ull : (unsigned long long)(seconds * 1e9);
+  int rc = tc_set_wait_limit(c, ns);
+  if (rc) return rc;
+  return oz_set_wait_limit(c, ns);
 }
 
 int dyson_set_sweep_variant(dyson_ctx* c, int variant) {

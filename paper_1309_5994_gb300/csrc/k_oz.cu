@@ -569,6 +569,12 @@ int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, do
   return DYSON_OK;
 }
 
+int oz_set_wait_limit(dyson_ctx* c, unsigned long long ns) {
+  DY_CUDA(c, cudaMemcpyToSymbolAsync(ptx::g_wait_limit_ns, &ns, sizeof ns, 0, cudaMemcpyHostToDevice, c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DYSON_OK;
+}
+
 int oz_check_error(dyson_ctx* c) {
   OzState* st = static_cast<OzState*>(c->oz);
   if (!st || !st->d_err) return DYSON_OK;

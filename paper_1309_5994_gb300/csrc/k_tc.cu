@@ -62,6 +62,7 @@ struct TcState {
   float* xbuf = nullptr;
   size_t xbuf_bytes = 0;
   int* d_err = nullptr;
+  int* h_err = nullptr;              // pinned copy of d_err (tc_error_enqueue / tc_error_status)
   bool smem_set = false;
   int num_sms = 0;
   // CTA-pair kernel: X map with half-width boxes, co-resident clusters (0 = unused)
@@ -1360,17 +1361,36 @@ int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, f
                          phases & (TC_GATHER | TC_GEMM), c->stream, &st->a_hi, &st->a_lo, &st->x, h, act, sweep);
 }
 
-int tc_check_error(dyson_ctx* c) {
+int tc_set_wait_limit(dyson_ctx* c, unsigned long long ns) {
+  DY_CUDA(c, cudaMemcpyToSymbolAsync(ptx::g_wait_limit_ns, &ns, sizeof ns, 0, cudaMemcpyHostToDevice, c->stream));
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  return DYSON_OK;
+}
+
+int tc_error_enqueue(dyson_ctx* c) {
   TcState* st = static_cast<TcState*>(c->tc);
   if (!st || !st->d_err) return DYSON_OK;
-  int h = 0;
-  DY_CUDA(c, cudaMemcpyAsync(&h, st->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  DY_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (h) {
-    cudaMemsetAsync(st->d_err, 0, sizeof(int), c->stream);
-    return ctx_fail(c, DYSON_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its time limit");
+  if (!st->h_err) {
+    DY_CUDA(c, cudaMallocHost((void**)&st->h_err, sizeof(int)));
+    *st->h_err = 0;
   }
+  DY_CUDA(c, cudaMemcpyAsync(st->h_err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   return DYSON_OK;
+}
+
+int tc_error_status(dyson_ctx* c) {
+  TcState* st = static_cast<TcState*>(c->tc);
+  if (!st || !st->h_err || !*st->h_err) return DYSON_OK;
+  *st->h_err = 0;
+  cudaMemsetAsync(st->d_err, 0, sizeof(int), c->stream);
+  return ctx_fail(c, DYSON_ERR_TIMEOUT, "a tensor-core pipeline wait exceeded its time limit");
+}
+
+int tc_check_error(dyson_ctx* c) {
+  int rc = tc_error_enqueue(c);
+  if (rc) return rc;
+  DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  return tc_error_status(c);
 }
 
 void tc_release(dyson_ctx* c) {
@@ -1378,6 +1398,7 @@ void tc_release(dyson_ctx* c) {
   if (!st) return;
   if (st->xbuf) cudaFree(st->xbuf);
   if (st->d_err) cudaFree(st->d_err);
+  if (st->h_err) cudaFreeHost(st->h_err);
   if (st->h_inst) cudaFreeHost(st->h_inst);
   if (st->d_inst) cudaFree(st->d_inst);
   delete st;

@@ -13,4 +13,6 @@ void oz_invalidate(dyson_ctx* c);
 int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, double tol);
 // DYSON_ERR_TIMEOUT if a bounded pipeline wait expired (clears the flag)
 int oz_check_error(dyson_ctx* c);
+// time limit (ns) of the pipeline waits of the residual kernels on the context's device
+int oz_set_wait_limit(dyson_ctx* c, unsigned long long ns);
 void oz_release(dyson_ctx* c);

@@ -32,16 +32,24 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false once the CTA abort flag is raised (when honour_abort) or after
-// limit_ns of %globaltimer, in which case the flag is raised.
+// Time limit of the pipeline waits (those that honour the abort flag), per device and
+// translation unit: 2 s unless set otherwise (dyson_set_wait_limit, for tests of the
+// timeout path).  The drain waits that let in-flight copies and MMAs land before a CTA
+// exits keep kDrainLimitNs whatever this is.
+static __device__ unsigned long long g_wait_limit_ns = 2000000000ull;
+constexpr unsigned long long kDrainLimitNs = 2000000000ull;
+
+// Bounded wait: false once the CTA abort flag is raised (when honour_abort) or after the
+// time limit of %globaltimer, in which case the flag is raised.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
-                                          bool honour_abort = true,
-                                          unsigned long long limit_ns = 2000000000ull) {
+                                          bool honour_abort = true) {
+  const unsigned long long limit_ns = honour_abort ? g_wait_limit_ns : kDrainLimitNs;
+  const bool every = limit_ns < 1000000ull;             // limits below 1 ms (tests): clock read on every poll
   unsigned long long t0 = gtimer();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(b, parity)) return true;
     if (honour_abort && *abort_flag) return false;
-    if ((it & 63) == 63 && gtimer() - t0 > limit_ns) {
+    if ((every || (it & 63) == 63) && gtimer() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -75,13 +83,14 @@ __device__ __forceinline__ bool mbar_try_cluster(uint64_t* b, uint32_t parity) {
 }
 // bounded wait with cluster-scope acquire, for barriers that the peer CTA arrives on
 __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* b, uint32_t parity, volatile int* abort_flag,
-                                                  bool honour_abort = true,
-                                                  unsigned long long limit_ns = 2000000000ull) {
+                                                  bool honour_abort = true) {
+  const unsigned long long limit_ns = honour_abort ? g_wait_limit_ns : kDrainLimitNs;
+  const bool every = limit_ns < 1000000ull;
   unsigned long long t0 = gtimer();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_cluster(b, parity)) return true;
     if (honour_abort && *abort_flag) return false;
-    if ((it & 63) == 63 && gtimer() - t0 > limit_ns) {
+    if ((every || (it & 63) == 63) && gtimer() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }

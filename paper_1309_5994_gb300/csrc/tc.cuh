@@ -51,8 +51,15 @@ enum { TC_GATHER = 1, TC_GEMM = 2, TC_TABLE_ONLY = 4 };
 constexpr int TC_TILE_COLS = 256;
 int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* d_in, float* d_out, int phases,
              const int* act = nullptr, int sweep = 0);
-// DYSON_ERR_TIMEOUT if a bounded pipeline wait of an earlier sweep expired (clears the flag)
+// DYSON_ERR_TIMEOUT if a bounded pipeline wait of an earlier sweep expired (clears the flag);
+// synchronises the context's stream
 int tc_check_error(dyson_ctx* c);
+// the same in two halves around a synchronisation the caller makes anyway: enqueue the
+// copy of the flag to pinned host memory, then, after the stream has synchronised, read it
+int tc_error_enqueue(dyson_ctx* c);
+// time limit (ns) of the pipeline waits of this file's kernels on the context's device
+int tc_set_wait_limit(dyson_ctx* c, unsigned long long ns);
+int tc_error_status(dyson_ctx* c);
 // free tensor-core module state
 void tc_release(dyson_ctx* c);
 
