@@ -166,10 +166,10 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
 // one 3xTF32 tensor-core sweep dout = r + K din with per-kind event timing: the
 // fused gather + GEMM launch, or the gather launch and the GEMM launch
 int tc_timed_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, const int* act,
-                   int sweep) {
+                   int sweep, int rform = TC_R_DENSE) {
   if (tc_uses_fused(c)) {
     KernelTimer t(c, DYSON_KERNEL_SWEEP_TC_FUSED);
-    return tc_sweep(c, ncol, gs, r, din, dout, TC_GATHER | TC_GEMM, act, sweep);
+    return tc_sweep(c, ncol, gs, r, din, dout, TC_GATHER | TC_GEMM, act, sweep, rform);
   }
   int rc;
   {
@@ -183,10 +183,11 @@ int tc_timed_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* 
 // inner solve d <- r + K d in FP32 (SIMT or 3xTF32 tensor cores)
 // act (optional): support truncation of the tensor-core sweeps (tc_sweep), valid
 // while every column of r32 is zero off its source site
+// r_on_sources: r32 is non-zero only on each column's source site (the first right-hand side)
 int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float* da, float* db, int max_sweeps,
                 const std::vector<double>& rref, float** dres, dyson_report* rep, double* peak_out,
                 double abort_peak = std::numeric_limits<double>::infinity(), const int* act = nullptr,
-                bool* exhausted = nullptr, double target = kInnerTarget) {
+                bool* exhausted = nullptr, double target = kInnerTarget, bool r_on_sources = false) {
   if (exhausted) *exhausted = false;
   const int ng = ncol / gs;
   const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
@@ -198,7 +199,9 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
   for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
     if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
-      if ((rc = tc_timed_sweep(c, ncol, gs, r32, da, db, act, sweep))) return rc;
+      if ((rc = tc_timed_sweep(c, ncol, gs, r32, da, db, act, sweep,
+                               r_on_sources ? TC_R_ON_SOURCES : TC_R_DENSE)))
+        return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
       launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, ncol, gs,
@@ -252,7 +255,7 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
 int matvec_f32(dyson_ctx* c, int ncol, int gs, int precision, const float* zero, const float* in, float* out) {
   int rc;
   if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
-    if ((rc = tc_timed_sweep(c, ncol, gs, zero, in, out, nullptr, 0))) return rc;
+    if ((rc = tc_timed_sweep(c, ncol, gs, zero, in, out, nullptr, 0, TC_R_ZERO))) return rc;
   } else {
     KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
     launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, zero, in, out, c->Nr, c->Nc, ncol, gs,
@@ -358,7 +361,7 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
       bool exhausted = false;
       rc = inner_solve(c, ncol, gs, precision, r32, da, db, max_sweeps, rref, &d, rep, &peak,
                        may_switch ? kSeriesPeakMax : std::numeric_limits<double>::infinity(), act, &exhausted,
-                       inner_target(kInnerTarget, tol, prev_res));
+                       inner_target(kInnerTarget, tol, prev_res), ref == 0);
       if (rc == DYSON_ERR_DIVERGED && may_switch) {
         gmres = true;                                    // redo this refinement with GMRES
         --ref;

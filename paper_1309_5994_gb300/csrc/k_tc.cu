@@ -226,7 +226,8 @@ __device__ __forceinline__ void split_tile(uint8_t* x, int tt) {
 // into norm[] per group of gs columns (gs a multiple of 32)
 // (CH = 32 or 16 columns per tcgen05.ld; 16 keeps the register count of the 512-thread
 // fused kernel below its limit)
-template <int CH = 32>
+// (RZERO: r is zero on this tile, its loads are skipped)
+template <int CH = 32, bool RZERO = false>
 __device__ __forceinline__ void epilogue_rows(uint32_t tacc, int mg, int n_first, int site, int ncol, int gs,
                                               size_t N2, const float* __restrict__ r, const float* __restrict__ din,
                                               float* __restrict__ dout, unsigned long long* __restrict__ norm,
@@ -251,7 +252,7 @@ __device__ __forceinline__ void epilogue_rows(uint32_t tacc, int mg, int n_first
     const size_t base = ((size_t)site * ncol + n0) * N2 + mg;
 #pragma unroll
     for (int j = 0; j < CH; ++j) {
-      rv[j] = __ldcs(r + base + (size_t)j * N2);
+      rv[j] = RZERO ? 0.f : __ldcs(r + base + (size_t)j * N2);
       dv[j] = __ldcs(din + base + (size_t)j * N2);
     }
     if (CH == 32) tmem_ld32(tacc + (uint32_t)(c * CH), v);
@@ -748,7 +749,8 @@ template <int GT>
 __global__ void __launch_bounds__(F_THREADS, 1)
     k_tc_fused(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
                const float* __restrict__ r, const float* __restrict__ din, float* __restrict__ dout,
-               const float* __restrict__ Jz, const int* __restrict__ nbr, const int* __restrict__ nbond, int Lx,
+               const int* __restrict__ rsrc, const float* __restrict__ Jz, const int* __restrict__ nbr,
+               const int* __restrict__ nbond, int Lx,
                int Ly, int Nc, int ncol, int gs, unsigned long long* __restrict__ norm, int* __restrict__ err,
                const int* __restrict__ act, int sweep) {
   using namespace ptx;
@@ -998,11 +1000,23 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       go = __all_sync(0xffffffffu, go);
       if (!go) break;
       tc_fence_after();
+      // r = 0 (a matvec), or r non-zero only on the rows of each column's source site
+      // (the first right-hand side Lambda delta_s) and no column of the tile has its
+      // source here: its loads are skipped
+      bool rz = r == nullptr;
+      if (!rz && rsrc) {
+        bool here = false;
+        for (int n = T.nt * BN + lane; n < min(ncol, T.nt * BN + BN); n += 32) here |= __ldg(rsrc + n) == T.site;
+        rz = !__any_sync(0xffffffffu, here);
+      }
 #pragma unroll
       for (int gi = 0; gi < GT; ++gi) {
         const uint32_t tacc = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)((buf * GT + gi) * BN);
         const int mg = (T.gt * GT + gi) * PM + (int)rank * BM + q4 * 32 + lane;
-        epilogue_rows<16>(tacc, mg, T.nt * BN, T.site, ncol, gs, (size_t)N2, r, din, dout, norm, lane);
+        if (rz)
+          epilogue_rows<16, true>(tacc, mg, T.nt * BN, T.site, ncol, gs, (size_t)N2, r, din, dout, norm, lane);
+        else
+          epilogue_rows<16, false>(tacc, mg, T.nt * BN, T.site, ncol, gs, (size_t)N2, r, din, dout, norm, lane);
       }
       tc_fence_before();
       mbar_arrive_remote(empty_bar0 + (uint32_t)(buf * sizeof(uint64_t)));
@@ -1183,7 +1197,7 @@ int tc_prepare(dyson_ctx* c, int ncol, bool need_x = true) {
 
 template <int GT>
 int launch_fused(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, const int* act,
-                 int sweep) {
+                 int sweep, const int* rsrc) {
   TcState* st = state(c);
   const long long tiles = (long long)c->Nr * ((ncol + BN - 1) / BN) * ((2 * c->Nc) / (PM * GT));
   const int pairs = (int)std::min<long long>(tiles, fused_clusters<GT>(c, st));
@@ -1199,7 +1213,7 @@ int launch_fused(dyson_ctx* c, int ncol, int gs, const float* r, const float* di
   cfg.stream = c->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  DY_CUDA(c, cudaLaunchKernelEx(&cfg, k_tc_fused<GT>, st->a_hi, st->a_lo, r, din, dout,
+  DY_CUDA(c, cudaLaunchKernelEx(&cfg, k_tc_fused<GT>, st->a_hi, st->a_lo, r, din, dout, rsrc,
                                 (const float*)c->d_Jz,
                                 (const int*)c->d_nbr, (const int*)c->d_nbond, c->Lx, c->Ly, c->Nc, ncol, gs,
                                 c->d_norm, st->d_err, act, sweep));
@@ -1290,15 +1304,17 @@ int tc_launch_table(dyson_ctx* c, const TcInst* d_tab, int ninst, int tiles, int
 }
 
 int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, int phases,
-             const int* act, int sweep) {
+             const int* act, int sweep, int rform) {
   const int gt = (phases & TC_TABLE_ONLY) ? 0 : fused_gt(c);
   int rc = tc_prepare(c, ncol, gt == 0);
   if (rc) return rc;
   if (gt > 0) {
     // one launch gathers and multiplies: the gather phase alone launches nothing
     if (!(phases & TC_GEMM)) return DYSON_OK;
-    return gt == 1 ? launch_fused<1>(c, ncol, gs, r, din, dout, act, sweep)
-                   : launch_fused<2>(c, ncol, gs, r, din, dout, act, sweep);
+    const float* rr = rform == TC_R_ZERO ? nullptr : r;
+    const int* rsrc = rform == TC_R_ON_SOURCES ? c->d_src_site : nullptr;
+    return gt == 1 ? launch_fused<1>(c, ncol, gs, rr, din, dout, act, sweep, rsrc)
+                   : launch_fused<2>(c, ncol, gs, rr, din, dout, act, sweep, rsrc);
   }
   TcState* st = state(c);
   const int Nc = c->Nc, N2 = 2 * Nc, Nr = c->Nr;

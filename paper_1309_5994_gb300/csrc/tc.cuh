@@ -47,10 +47,14 @@ bool tc_uses_fused(dyson_ctx* c);
 // act (optional, device [Nr][ceil(ncol / 256)]): support truncation (App. C, Sec. IV.D):
 // the first sweep at which each (site, 256-column tile) can be non-zero; tiles with
 // act > sweep are skipped, so their d_out must already hold zeros.
+// rform: what the caller knows of r, for the fused kernel to skip loads of zeros:
+// TC_R_DENSE (general), TC_R_ZERO (r = 0: a matvec), TC_R_ON_SOURCES (r non-zero only
+// on the rows of each column's source site, c->d_src_site: the first right-hand side)
 enum { TC_GATHER = 1, TC_GEMM = 2, TC_TABLE_ONLY = 4 };
+enum { TC_R_DENSE = 0, TC_R_ZERO = 1, TC_R_ON_SOURCES = 2 };
 constexpr int TC_TILE_COLS = 256;
 int tc_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* d_in, float* d_out, int phases,
-             const int* act = nullptr, int sweep = 0);
+             const int* act = nullptr, int sweep = 0, int rform = TC_R_DENSE);
 // DYSON_ERR_TIMEOUT if a bounded pipeline wait of an earlier sweep expired (clears the flag);
 // synchronises the context's stream
 int tc_check_error(dyson_ctx* c);
