@@ -713,6 +713,15 @@ constexpr int F_EPI_W0 = 12;
 constexpr int F_A_GROUP = 2 * A_TILE;                   // Lambda hi + lo, one row group, this CTA's 128 rows
 constexpr int F_SITE_BAND = 2;                          // lattice rows per band of the site order
 constexpr int F_RELAY_W = 2;                            // warp 2: relays "Lambda landed" to the even CTA
+// registers per thread of each warpgroup once the roles split: the producers keep sixteen
+// neighbour loads in flight one k-block ahead, more than the 128 a thread of a 512-thread
+// block gets at launch; the TMA / MMA / relay warpgroup needs few
+constexpr int F_REG_CTRL = 56, F_REG_PROD = 168, F_REG_EPI = 120;
+constexpr int F_REGS_AT_LAUNCH = 65536 / F_THREADS;
+static_assert(F_REG_CTRL + 2 * F_REG_PROD + F_REG_EPI <= 4 * F_REGS_AT_LAUNCH,
+              "the warpgroups' register shares exceed the block's registers at launch");
+static_assert(F_PROD_W0 == 4 && F_PROD_WARPS == 8 && F_EPI_W0 == 12 && F_THREADS == 512,
+              "the register split assumes warpgroups {0-3: control, 4-11: producers, 12-15: epilogue}");
 template <int GT>
 struct FusedCfg {
   static constexpr int STAGE = GT * F_A_GROUP + 2 * PX_TILE;
@@ -795,97 +804,122 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   volatile int* abort_p = &abort_flag;
   auto stage_ptr = [&](int s) { return smem + (size_t)s * STAGE; };
 
-  if (warp == 0) {
-    if (lane == 0) {
-      // ---------------- TMA: Lambda hi / lo (each CTA its own rows) ----------------
-      int g = 0;
-      bool ok = true;
-      for (int tile = pair; tile < tiles && ok; tile += npairs) {
-        const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
-        if (!T.active) continue;
-        int t2 = tile + npairs;
-        FTile N;
-        N.active = false;
-        for (; t2 < tiles; t2 += npairs) {
-          N = fused_tile(t2, NGT, NT, Lx, Ly, act, sweep);
-          if (N.active) break;
-        }
-        for (int kb = 0; kb < KB; ++kb, ++g) {
-          const int s = g % STAGES;
-          if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1, abort_p)) {
-            ok = false;
-            break;
+  // each warpgroup sets its register budget first, in its own branch, so that the code of
+  // each role is compiled against that budget
+  if (warp < F_PROD_W0) {
+    reg_release<F_REG_CTRL>();
+    if (warp == 0) {
+      if (lane == 0) {
+        // ---------------- TMA: Lambda hi / lo (each CTA its own rows) ----------------
+        int g = 0;
+        bool ok = true;
+        for (int tile = pair; tile < tiles && ok; tile += npairs) {
+          const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
+          if (!T.active) continue;
+          int t2 = tile + npairs;
+          FTile N;
+          N.active = false;
+          for (; t2 < tiles; t2 += npairs) {
+            N = fused_tile(t2, NGT, NT, Lx, Ly, act, sweep);
+            if (N.active) break;
           }
-          uint8_t* st = stage_ptr(s);
-          mbar_expect_tx(&full_a[s], GT * F_A_GROUP);
-#pragma unroll
-          for (int gi = 0; gi < GT; ++gi) {
-            const int row0 = (T.gt * GT + gi) * PM + (int)rank * BM;
-            tma_load_3d(st + gi * F_A_GROUP, &map_ahi, &full_a[s], kb * BK, row0, T.site);
-            tma_load_3d(st + gi * F_A_GROUP + A_TILE, &map_alo, &full_a[s], kb * BK, row0, T.site);
-          }
-          const int ahead = kb + PREFETCH;
-          const FTile* P = ahead < KB ? &T : (N.active && ahead - KB < KB ? &N : nullptr);
-          if (P) {
-            const int k2 = ahead < KB ? ahead : ahead - KB;
-#pragma unroll
+          for (int kb = 0; kb < KB; ++kb, ++g) {
+            const int s = g % STAGES;
+            if (g >= STAGES && !mbar_wait(&empty[s], ((g / STAGES) - 1) & 1, abort_p)) {
+              ok = false;
+              break;
+            }
+            uint8_t* st = stage_ptr(s);
+            mbar_expect_tx(&full_a[s], GT * F_A_GROUP);
+  #pragma unroll
             for (int gi = 0; gi < GT; ++gi) {
-              const int row0 = (P->gt * GT + gi) * PM + (int)rank * BM;
-              tma_prefetch_3d(&map_ahi, k2 * BK, row0, P->site);
-              tma_prefetch_3d(&map_alo, k2 * BK, row0, P->site);
+              const int row0 = (T.gt * GT + gi) * PM + (int)rank * BM;
+              tma_load_3d(st + gi * F_A_GROUP, &map_ahi, &full_a[s], kb * BK, row0, T.site);
+              tma_load_3d(st + gi * F_A_GROUP + A_TILE, &map_alo, &full_a[s], kb * BK, row0, T.site);
+            }
+            const int ahead = kb + PREFETCH;
+            const FTile* P = ahead < KB ? &T : (N.active && ahead - KB < KB ? &N : nullptr);
+            if (P) {
+              const int k2 = ahead < KB ? ahead : ahead - KB;
+  #pragma unroll
+              for (int gi = 0; gi < GT; ++gi) {
+                const int row0 = (P->gt * GT + gi) * PM + (int)rank * BM;
+                tma_prefetch_3d(&map_ahi, k2 * BK, row0, P->site);
+                tma_prefetch_3d(&map_alo, k2 * BK, row0, P->site);
+              }
             }
           }
         }
+        for (int q = g > STAGES ? g - STAGES : 0; q < g; ++q)
+          mbar_wait(&full_a[q % STAGES], (q / STAGES) & 1, abort_p, false);
       }
-      for (int q = g > STAGES ? g - STAGES : 0; q < g; ++q)
-        mbar_wait(&full_a[q % STAGES], (q / STAGES) & 1, abort_p, false);
-    }
-  } else if (warp == 1) {
-    if (lane == 0 && rank == 0) {
-      // ---------------- MMA issuer (even CTA) ----------------
-      int g = 0, t = 0;
-      bool ok = true, any = false;
-      for (int tile = pair; tile < tiles && ok; tile += npairs) {
-        const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
-        if (!T.active) continue;
-        const int buf = t % NBUF;
-        if (t >= NBUF && !mbar_wait_cluster(&acc_empty[buf], ((t / NBUF) - 1) & 1, abort_p)) break;
-        ++t;
-        tc_fence_after();
-        for (int kb = 0; kb < KB; ++kb, ++g) {
-          const int s = g % STAGES;
-          if (!mbar_wait_cluster(&full[s], (g / STAGES) & 1, abort_p)) {
-            ok = false;
-            break;
-          }
+    } else if (warp == 1) {
+      if (lane == 0 && rank == 0) {
+        // ---------------- MMA issuer (even CTA) ----------------
+        int g = 0, t = 0;
+        bool ok = true, any = false;
+        for (int tile = pair; tile < tiles && ok; tile += npairs) {
+          const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
+          if (!T.active) continue;
+          const int buf = t % NBUF;
+          if (t >= NBUF && !mbar_wait_cluster(&acc_empty[buf], ((t / NBUF) - 1) & 1, abort_p)) break;
+          ++t;
           tc_fence_after();
-          const uint32_t st = smem_u32(stage_ptr(s));
-          const uint32_t x_hi = st + GT * F_A_GROUP, x_lo = x_hi + PX_TILE;
-#pragma unroll
-          for (int k8 = 0; k8 < BK / 8; ++k8) {
-            const uint32_t off = k8 * 32;
-            const uint64_t dxh = sdesc_sw128(x_hi + off), dxl = sdesc_sw128(x_lo + off);
-#pragma unroll
-            for (int gi = 0; gi < GT; ++gi) {
-              const uint32_t a_hi = st + gi * F_A_GROUP, a_lo = a_hi + A_TILE;
-              const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
-              const uint32_t dacc = tmem + (uint32_t)((buf * GT + gi) * BN);
-              mma_pair_tf32(dacc, dah, dxh, P_IDESC, (kb | k8) ? 1u : 0u);
-              mma_pair_tf32(dacc, dah, dxl, P_IDESC, 1u);
-              mma_pair_tf32(dacc, dal, dxh, P_IDESC, 1u);
+          for (int kb = 0; kb < KB; ++kb, ++g) {
+            const int s = g % STAGES;
+            if (!mbar_wait_cluster(&full[s], (g / STAGES) & 1, abort_p)) {
+              ok = false;
+              break;
             }
+            tc_fence_after();
+            const uint32_t st = smem_u32(stage_ptr(s));
+            const uint32_t x_hi = st + GT * F_A_GROUP, x_lo = x_hi + PX_TILE;
+  #pragma unroll
+            for (int k8 = 0; k8 < BK / 8; ++k8) {
+              const uint32_t off = k8 * 32;
+              const uint64_t dxh = sdesc_sw128(x_hi + off), dxl = sdesc_sw128(x_lo + off);
+  #pragma unroll
+              for (int gi = 0; gi < GT; ++gi) {
+                const uint32_t a_hi = st + gi * F_A_GROUP, a_lo = a_hi + A_TILE;
+                const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
+                const uint32_t dacc = tmem + (uint32_t)((buf * GT + gi) * BN);
+                mma_pair_tf32(dacc, dah, dxh, P_IDESC, (kb | k8) ? 1u : 0u);
+                mma_pair_tf32(dacc, dah, dxl, P_IDESC, 1u);
+                mma_pair_tf32(dacc, dal, dxh, P_IDESC, 1u);
+              }
+            }
+            mma_commit_pair_mc(&empty[s], 0x3);
+            any = true;
           }
-          mma_commit_pair_mc(&empty[s], 0x3);
-          any = true;
+          if (ok) mma_commit_pair_mc(&acc_full[buf], 0x3);
         }
-        if (ok) mma_commit_pair_mc(&acc_full[buf], 0x3);
+        if (any) {
+          mma_commit_pair_mc(&drain, 0x1);
+          mbar_wait(&drain, 0, abort_p, false);
+        }
       }
-      if (any) {
-        mma_commit_pair_mc(&drain, 0x1);
-        mbar_wait(&drain, 0, abort_p, false);
+    } else if (warp == F_RELAY_W) {
+      if (lane == 0) {
+        // ---------------- relay: this CTA's stage complete -> even CTA's stage barrier ----------------
+        const uint32_t full_bar0 = mapa(smem_u32(&full[0]), 0);
+        int g = 0;
+        bool ok = true;
+        for (int tile = pair; tile < tiles && ok; tile += npairs) {
+          const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
+          if (!T.active) continue;
+          for (int kb = 0; kb < KB; ++kb, ++g) {
+            const int s = g % STAGES;
+            if (!mbar_wait(&full_a[s], (g / STAGES) & 1, abort_p) || !mbar_wait(&xready[s], (g / STAGES) & 1, abort_p)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_remote(full_bar0 + (uint32_t)(s * 8));
+          }
+        }
       }
     }
-  } else if (warp >= F_PROD_W0 && warp < F_PROD_W0 + F_PROD_WARPS) {
+  } else if (warp < F_EPI_W0) {
+    reg_claim<F_REG_PROD>();
     // ---------------- gather producers (both CTAs) ----------------
     // thread pt: 16-byte chunk j of the k-block row (k = 32 kb + 4 j .. + 3) for the
     // tile columns c0 + 32 i, i = 0..3, of this CTA's half
@@ -967,26 +1001,8 @@ __global__ void __launch_bounds__(F_THREADS, 1)
         if (lane == 0) mbar_arrive(&xready[s]);
       }
     }
-  } else if (warp == F_RELAY_W) {
-    if (lane == 0) {
-      // ---------------- relay: this CTA's stage complete -> even CTA's stage barrier ----------------
-      const uint32_t full_bar0 = mapa(smem_u32(&full[0]), 0);
-      int g = 0;
-      bool ok = true;
-      for (int tile = pair; tile < tiles && ok; tile += npairs) {
-        const FTile T = fused_tile(tile, NGT, NT, Lx, Ly, act, sweep);
-        if (!T.active) continue;
-        for (int kb = 0; kb < KB; ++kb, ++g) {
-          const int s = g % STAGES;
-          if (!mbar_wait(&full_a[s], (g / STAGES) & 1, abort_p) || !mbar_wait(&xready[s], (g / STAGES) & 1, abort_p)) {
-            ok = false;
-            break;
-          }
-          mbar_arrive_remote(full_bar0 + (uint32_t)(s * 8));
-        }
-      }
-    }
-  } else if (warp >= F_EPI_W0) {
+  } else {
+    reg_release<F_REG_EPI>();
     // ---------------- epilogue (both CTAs, own 128 rows of each group) ----------------
     const int q4 = warp - F_EPI_W0;
     const uint32_t empty_bar0 = mapa(smem_u32(&acc_empty[0]), 0);
@@ -1102,6 +1118,11 @@ int fused_clusters(dyson_ctx* c, TcState* st) {
   n = 0;
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) sms = 0;
+  // the warpgroups' register shares add up to exactly F_REGS_AT_LAUNCH per thread: with
+  // any other count at launch the producers' increase could not be met, so the kernel is
+  // not offered
+  cudaFuncAttributes fa = {};
+  if (cudaFuncGetAttributes(&fa, k_tc_fused<GT>) != cudaSuccess || fa.numRegs != F_REGS_AT_LAUNCH) sms = 0;
   if (sms >= 2 && cudaFuncSetAttribute(k_tc_fused<GT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        FusedCfg<GT>::SMEM) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};

@@ -223,4 +223,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// per-warpgroup register budgets (every warp of a warpgroup executes the same one): the
+// shares of all warpgroups must add up to at most the block's registers at launch, or an
+// increase waits for registers that are never released
+template <uint32_t N>
+__device__ __forceinline__ void reg_release() {
+  static_assert(N >= 24 && N <= 256 && N % 8 == 0, "setmaxnreg takes 24..256 in steps of 8");
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <uint32_t N>
+__device__ __forceinline__ void reg_claim() {
+  static_assert(N >= 24 && N <= 256 && N % 8 == 0, "setmaxnreg takes 24..256 in steps of 8");
+  asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
+
 }  // namespace ptx
