@@ -807,7 +807,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   // each warpgroup sets its register budget first, in its own branch, so that the code of
   // each role is compiled against that budget
   if (warp < F_PROD_W0) {
-    reg_release<F_REG_CTRL>();
+    reg_budget<F_REG_CTRL, F_REGS_AT_LAUNCH>();
     if (warp == 0) {
       if (lane == 0) {
         // ---------------- TMA: Lambda hi / lo (each CTA its own rows) ----------------
@@ -919,7 +919,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       }
     }
   } else if (warp < F_EPI_W0) {
-    reg_claim<F_REG_PROD>();
+    reg_budget<F_REG_PROD, F_REGS_AT_LAUNCH>();
     // ---------------- gather producers (both CTAs) ----------------
     // thread pt: 16-byte chunk j of the k-block row (k = 32 kb + 4 j .. + 3) for the
     // tile columns c0 + 32 i, i = 0..3, of this CTA's half
@@ -1002,7 +1002,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       }
     }
   } else {
-    reg_release<F_REG_EPI>();
+    reg_budget<F_REG_EPI, F_REGS_AT_LAUNCH>();
     // ---------------- epilogue (both CTAs, own 128 rows of each group) ----------------
     const int q4 = warp - F_EPI_W0;
     const uint32_t empty_bar0 = mapa(smem_u32(&acc_empty[0]), 0);

@@ -236,5 +236,13 @@ __device__ __forceinline__ void reg_claim() {
   static_assert(N >= 24 && N <= 256 && N % 8 == 0, "setmaxnreg takes 24..256 in steps of 8");
   asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
 }
+// a warpgroup's budget N from the AT_LAUNCH registers a thread starts with: a decrease
+// may only lower the count and an increase only raise it, so the instruction follows
+// from the two counts (none where they are equal)
+template <uint32_t N, uint32_t AT_LAUNCH>
+__device__ __forceinline__ void reg_budget() {
+  if constexpr (N < AT_LAUNCH) reg_release<N>();
+  else if constexpr (N > AT_LAUNCH) reg_claim<N>();
+}
 
 }  // namespace ptx
