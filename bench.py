@@ -142,7 +142,8 @@ def bench_config(args, p, world):
             f"profiling case, not the benchmark: {args.lattice}x{args.lattice} lattice on the same contour",
             "block_columns_per_step_per_gpu": args.batch, "tol_rel_residual": args.tol,
             "lattice": [p.Lx, p.Ly], "Nc": p.Nc,
-            "l2": f"inputs larger than L2: {48 * p.Nr * p.Nc * p.Nc * args.batch / 1e9:.1f} GB of state per step",
+            # complex128 G, FP32 right-hand side and two FP32 states per vector column and site
+            "l2": f"inputs larger than L2: {40 * p.Nr * p.Nc * p.Nc * args.batch / 1e9:.1f} GB of state per step",
             "parallelism": f"block columns sharded over {world} GPU(s), no data-path collective"}
 
 

@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   constexpr int STAGES = OzPipe<SE>::STAGES, STAGE_BYTES = OzPipe<SE>::STAGE_BYTES;
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tmem_holder;
-  __shared__ int abort_flag;
+  __shared__ WaitCtl wctl;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N2 = 2 * Nc, KB = N2 / BK;
   const int MT = N2 / BM, NT = (ncol + BN - 1) / BN;
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&acc_empty[b], 256);                   // 8 epilogue warps
     }
     mbar_init(&drain, 1);
-    abort_flag = 0;
+    wait_ctl_init(&wctl);
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(&tmem_holder, TMEM_COLS);
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
-  volatile int* abort_p = &abort_flag;
+  volatile WaitCtl* abort_p = &wctl;
   auto stage_ptr = [&](int s) { return smem + (size_t)s * STAGE_BYTES; };
 
   if (warp == 0) {
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
-  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+  if (threadIdx.x == 0 && wctl.abort) atomicExch(err, 1);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {

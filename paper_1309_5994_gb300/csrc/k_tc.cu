@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ __align__(8) uint64_t full_tma[STAGES], full_split[STAGES], empty[STAGES];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tmem_holder;
-  __shared__ int abort_flag;
+  __shared__ WaitCtl wctl;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&acc_empty[b], 128);
     }
     mbar_init(&drain, 1);
-    abort_flag = 0;
+    wait_ctl_init(&wctl);
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(&tmem_holder, TMEM_COLS);
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
-  volatile int* abort_p = &abort_flag;
+  volatile WaitCtl* abort_p = &wctl;
   auto stage_ptr = [&](int s) { return smem + (size_t)s * STAGE_BYTES; };
 
   if (warp == 0) {
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
-  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+  if (threadIdx.x == 0 && wctl.abort) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ __align__(8) uint64_t full_tma[P_STAGES], full_split[P_STAGES], empty[P_STAGES];
   __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], drain;
   __shared__ uint32_t tmem_holder;
-  __shared__ int abort_flag;
+  __shared__ WaitCtl wctl;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_ctarank();
@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&acc_empty[b], 256);                    // 128 epilogue threads of each CTA
     }
     mbar_init(&drain, 1);
-    abort_flag = 0;
+    wait_ctl_init(&wctl);
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc_pair(&tmem_holder, TMEM_COLS);
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   cluster_sync();                                       // the peer's barriers exist before any remote arrive
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
-  volatile int* abort_p = &abort_flag;
+  volatile WaitCtl* abort_p = &wctl;
   auto stage_ptr = [&](int s) { return smem + (size_t)s * P_STAGE_BYTES; };
 
   if (warp == 0) {
@@ -675,7 +675,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     tmem_dealloc_pair(tmem, TMEM_COLS);
   }
-  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+  if (threadIdx.x == 0 && wctl.abort) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -770,7 +770,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   __shared__ __align__(8) uint64_t full_a[STAGES], xready[STAGES], full[STAGES], empty[STAGES];
   __shared__ __align__(8) uint64_t acc_full[NBUF], acc_empty[NBUF], drain;
   __shared__ uint32_t tmem_holder;
-  __shared__ int abort_flag;
+  __shared__ WaitCtl wctl;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = cluster_ctarank();
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
       mbar_init(&acc_empty[b], 256);                    // 128 epilogue threads of each CTA
     }
     mbar_init(&drain, 1);
-    abort_flag = 0;
+    wait_ctl_init(&wctl);
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc_pair(&tmem_holder, TMEM_COLS);
@@ -801,7 +801,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
   cluster_sync();
   tc_fence_after();
   const uint32_t tmem = tmem_holder;
-  volatile int* abort_p = &abort_flag;
+  volatile WaitCtl* abort_p = &wctl;
   auto stage_ptr = [&](int s) { return smem + (size_t)s * STAGE; };
 
   // each warpgroup sets its register budget first, in its own branch, so that the code of
@@ -831,7 +831,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             }
             uint8_t* st = stage_ptr(s);
             mbar_expect_tx(&full_a[s], GT * F_A_GROUP);
-  #pragma unroll
+#pragma unroll
             for (int gi = 0; gi < GT; ++gi) {
               const int row0 = (T.gt * GT + gi) * PM + (int)rank * BM;
               tma_load_3d(st + gi * F_A_GROUP, &map_ahi, &full_a[s], kb * BK, row0, T.site);
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             const FTile* P = ahead < KB ? &T : (N.active && ahead - KB < KB ? &N : nullptr);
             if (P) {
               const int k2 = ahead < KB ? ahead : ahead - KB;
-  #pragma unroll
+#pragma unroll
               for (int gi = 0; gi < GT; ++gi) {
                 const int row0 = (P->gt * GT + gi) * PM + (int)rank * BM;
                 tma_prefetch_3d(&map_ahi, k2 * BK, row0, P->site);
@@ -874,11 +874,11 @@ __global__ void __launch_bounds__(F_THREADS, 1)
             tc_fence_after();
             const uint32_t st = smem_u32(stage_ptr(s));
             const uint32_t x_hi = st + GT * F_A_GROUP, x_lo = x_hi + PX_TILE;
-  #pragma unroll
+#pragma unroll
             for (int k8 = 0; k8 < BK / 8; ++k8) {
               const uint32_t off = k8 * 32;
               const uint64_t dxh = sdesc_sw128(x_hi + off), dxl = sdesc_sw128(x_lo + off);
-  #pragma unroll
+#pragma unroll
               for (int gi = 0; gi < GT; ++gi) {
                 const uint32_t a_hi = st + gi * F_A_GROUP, a_lo = a_hi + A_TILE;
                 const uint64_t dah = sdesc_sw128(a_hi + off), dal = sdesc_sw128(a_lo + off);
@@ -1047,7 +1047,7 @@ __global__ void __launch_bounds__(F_THREADS, 1)
     tc_fence_after();
     tmem_dealloc_pair(tmem, TMEM_COLS);
   }
-  if (threadIdx.x == 0 && abort_flag) atomicExch(err, 1);
+  if (threadIdx.x == 0 && wctl.abort) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------------------

@@ -39,18 +39,34 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 static __device__ unsigned long long g_wait_limit_ns = 2000000000ull;
 constexpr unsigned long long kDrainLimitNs = 2000000000ull;
 
+// Per-CTA state of the bounded waits, in shared memory: the abort flag, and the time limit,
+// copied from g_wait_limit_ns once when the CTA starts.  A wait thus reads no global memory:
+// a global load issued behind a thread's own outstanding loads would hold up the wait by
+// their latency, also when the barrier has long completed.
+struct WaitCtl {
+  unsigned long long limit_ns;
+  int abort;
+};
+__device__ __forceinline__ void wait_ctl_init(WaitCtl* w) {
+  w->limit_ns = g_wait_limit_ns;
+  w->abort = 0;
+}
+
 // Bounded wait: false once the CTA abort flag is raised (when honour_abort) or after the
-// time limit of %globaltimer, in which case the flag is raised.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+// time limit of %globaltimer, in which case the flag is raised.  A barrier that has already
+// completed costs one poll (no clock read).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile WaitCtl* w,
                                           bool honour_abort = true) {
-  const unsigned long long limit_ns = honour_abort ? g_wait_limit_ns : kDrainLimitNs;
+  if (mbar_try(b, parity)) return true;
+  unsigned long long limit_ns = kDrainLimitNs;
+  if (honour_abort) limit_ns = w->limit_ns;
   const bool every = limit_ns < 1000000ull;             // limits below 1 ms (tests): clock read on every poll
-  unsigned long long t0 = gtimer();
+  const unsigned long long t0 = gtimer();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(b, parity)) return true;
-    if (honour_abort && *abort_flag) return false;
+    if (honour_abort && w->abort) return false;
     if ((every || (it & 63) == 63) && gtimer() - t0 > limit_ns) {
-      *abort_flag = 1;
+      w->abort = 1;
       return false;
     }
   }
@@ -82,16 +98,18 @@ __device__ __forceinline__ bool mbar_try_cluster(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 // bounded wait with cluster-scope acquire, for barriers that the peer CTA arrives on
-__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* b, uint32_t parity, volatile WaitCtl* w,
                                                   bool honour_abort = true) {
-  const unsigned long long limit_ns = honour_abort ? g_wait_limit_ns : kDrainLimitNs;
+  if (mbar_try_cluster(b, parity)) return true;
+  unsigned long long limit_ns = kDrainLimitNs;
+  if (honour_abort) limit_ns = w->limit_ns;
   const bool every = limit_ns < 1000000ull;
-  unsigned long long t0 = gtimer();
+  const unsigned long long t0 = gtimer();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try_cluster(b, parity)) return true;
-    if (honour_abort && *abort_flag) return false;
+    if (honour_abort && w->abort) return false;
     if ((every || (it & 63) == 63) && gtimer() - t0 > limit_ns) {
-      *abort_flag = 1;
+      w->abort = 1;
       return false;
     }
   }
