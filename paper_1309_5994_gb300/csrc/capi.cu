@@ -479,6 +479,9 @@ int dyson_init(dyson_ctx** out, const dyson_lattice* L, const dyson_contour* C, 
       delete c;
       return fail_noctx(DYSON_ERR_INVALID_ARG, "J table holds a non-finite value");
     }
+  c->j_uniform = true;
+  for (int b = 1; b < c->Nb && c->j_uniform; ++b)
+    c->j_uniform = std::equal(c->J.begin() + (size_t)b * c->Nt, c->J.begin() + (size_t)(b + 1) * c->Nt, c->J.begin());
 
   // neighbour slots (+x, -x, +y, -y) with their bond indices
   std::vector<int> nbr((size_t)c->Nr * 4, -1), nbond((size_t)c->Nr * 4, -1);

@@ -99,6 +99,7 @@ struct dyson_ctx {
   int Lx = 0, Ly = 0, Nr = 0, Nb = 0, Nt = 0, Nm = 0, Nc = 0;
   double dt = 0, beta = 0, curvature = 0, mu = 0;
   std::vector<double> U, J;          // host copies of the drive tables
+  bool j_uniform = false;            // every bond carries the same J(t) row
 
   // device tables
   double* dU = nullptr;              // [Nr][Nt]

@@ -15,9 +15,9 @@
 // rounded at 2^-24 of its own size (about 2^-48 of the result).  The epilogue
 // adds them in FP64, rescales, and forms r = B + A X - G in FP64.  Solves whose
 // tolerance is 1e-8 or looser use the first five slices of each operand and the
-// 15 products with s + t <= 6 (digits are peeled from the top, so five slices are
-// the same numbers; truncation ~2^-35 of |A||X|, two orders below such a
-// tolerance).
+// 15 products with s + t <= 6 (X is split into five digits rounded at 2^-35 of its
+// column scale, the Lambda slices are the first five of seven; truncation ~2^-35 of
+// |A||X|, two orders below such a tolerance).
 //
 // Kernels: k_oz_aprep (once per Lambda), k_oz_xprep (gather + scale + slice of X
 // per residual), k_oz_gemm (persistent: TMA + tcgen05.mma kind::f16 into two
@@ -92,39 +92,44 @@ __device__ __forceinline__ double pow2_scale(double mx) {
 
 constexpr int FIX = 7 * S;                                 // fixed-point bits of a scaled value
 
-// Write the S slices of the fixed-point integer V = rint(x 2^FIX / sc) (|x| <= sc, sc a
-// power of two, |V| <= 2^FIX): V is cut into signed 7-bit digits with integer shifts,
-// slice s holds q_s 2^{-7 s}, q_s = round(V_rem / 2^{7 (S - s)}), |q_1| <= 128, |q_s| <= 64.
-__device__ __forceinline__ void write_digits(long long V, __nv_bfloat16* dst, size_t slice_stride, int nslices) {
-#pragma unroll
-  for (int s = 1; s <= S; ++s) {
-    const int sh = 7 * (S - s);
-    const long long q = sh ? ((V + (1LL << (sh - 1))) >> sh) : V;
-    V -= q << sh;
-    const float part = __int2float_rn((int)q) * __int_as_float((127 - 7 * s) << 23);   // q * 2^{-7 s}, exact
-    if (s <= nslices) dst[(size_t)(s - 1) * slice_stride] = __float2bfloat16_rn(part);
-  }
-}
+// the S slices of x (|x| <= sc, fix_over_sc = 2^FIX / sc): the fixed-point integer from one
+// FP64 multiply and one conversion (the Lambda slices, built once)
+__device__ __forceinline__ long long lambda_fixed(double x, double fix_over_sc) { return __double2ll_rn(x * fix_over_sc); }
 
-// the same with V from one FP64 multiply and one conversion (the Lambda slices, built once)
-__device__ __forceinline__ void write_slices(double x, double fix_over_sc, __nv_bfloat16* dst, size_t slice_stride,
-                                             int nslices = S) {
-  write_digits(__double2ll_rn(x * fix_over_sc), dst, slice_stride, nslices);
-}
-
-// rint(x 2^k) (|x 2^k| <= 2^FIX) by integer arithmetic on the bits of x, ties rounded away
-// from zero: the FP64 pipe is the scarce one in the slicing of X
-__device__ __forceinline__ long long scaled_to_fixed(double x, int k) {
+// rint(x 2^k) where the scaling only shifts right (E - 1075 + k <= 0, i.e. |x 2^k| < 2^52):
+// the mantissa shifted right by r with the half unit added first (ties away from zero).
+// Every caller's column scale is at least the column's largest value, so this holds there.
+__device__ __forceinline__ long long fixed_right(double x, int k) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((b >> 52) & 0x7FF);
-  if (E == 0) return 0;                                    // zero, or a denormal far below 2^-FIX of the scale
-  const long long M = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));
-  const int sh = E - 1075 + k;                             // x 2^k = M 2^sh
-  long long v;
-  if (sh >= 0) v = M << sh;                                // |x 2^k| <= 2^FIX keeps this below 2^63
-  else if (sh > -63) v = (M + (1ll << (-sh - 1))) >> (-sh);
-  else v = 0;
+  const unsigned long long M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int r = min(1075 - k - E, 63);                     // >= 0 by the condition above
+  const long long v = E == 0 ? 0 : (long long)((M + ((1ull << r) >> 1)) >> r);
   return (b >> 63) ? -v : v;
+}
+
+// The first NS signed 7-bit digits of V (|V| <= 2^FIX) in one pass: for A = |V| plus 64 in
+// every digit position below the top (and half a unit of the last kept digit when NS < S),
+// digit s of A in base 128, less 64, is the balanced digit q_s in [-64, 63]; the top digit
+// is A >> 7 (S - 1) <= 128.  Then sum_s q_s 2^{7 (S - s)} = |V| rounded to the last kept
+// digit, and the digits of V are those of |V| with its sign.  Slice s holds q_s 2^{-7 s}.
+template <int NS>
+__device__ __forceinline__ void write_digits_fast(long long V, __nv_bfloat16* dst, size_t slice_stride) {
+  static_assert(NS >= 1 && NS <= S, "digits kept");
+  constexpr unsigned long long BIAS = [] {
+    unsigned long long b = NS < S ? 1ull << (7 * (S - NS) - 1) : 0ull;
+    for (int s = 2; s <= NS; ++s) b += 64ull << (7 * (S - s));
+    return b;
+  }();
+  const bool neg = V < 0;
+  const unsigned long long A = (unsigned long long)(neg ? -V : V) + BIAS;
+#pragma unroll
+  for (int s = 1; s <= NS; ++s) {
+    const int sh = 7 * (S - s);
+    const int q = s == 1 ? (int)(A >> sh) : (int)((A >> sh) & 127u) - 64;
+    const float unit = __int_as_float((127 - 7 * s) << 23);                    // 2^{-7 s}
+    dst[(size_t)(s - 1) * slice_stride] = __float2bfloat16_rn(__int2float_rn(neg ? -q : q) * unit);
+  }
 }
 
 // Accumulator A of the slice products holds, for A < NACC - 1, sum q_s q_t 2^{-7 d} over
@@ -151,9 +156,11 @@ __device__ __forceinline__ double emb_value(const double2* lrow, int k, int part
   return part == kpart ? v.x : (part == 0 ? -v.y : v.y);
 }
 
-// one warp per row (site i, row m) of the embedding of Lambda W
-__global__ void k_oz_aprep(const double2* __restrict__ lam, int Nr, int Nt, int Nm, double dt, double beta,
-                           __nv_bfloat16* __restrict__ as, double* __restrict__ sigma) {
+// one warp per row (site i, row m) of the embedding of Lambda W; with Jrow set (hopping equal
+// on every bond), column k also carries the factor J(t(k)) that the gather would apply to
+// row k of X, so that X becomes the plain sum of the neighbours' columns
+__global__ void k_oz_aprep(const double2* __restrict__ lam, const double* __restrict__ Jrow, int Nr, int Nt, int Nm,
+                           double dt, double beta, __nv_bfloat16* __restrict__ as, double* __restrict__ sigma) {
   const int Nc = 2 * Nt + Nm, N2 = 2 * Nc;
   const size_t row = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
@@ -161,25 +168,32 @@ __global__ void k_oz_aprep(const double2* __restrict__ lam, int Nr, int Nt, int 
   const int i = (int)(row / N2), m = (int)(row % N2);
   const int z = m % Nc, part = m / Nc;
   const double2* lrow = lam + ((size_t)i * Nc + z) * Nc;
+  auto value = [&](int k) {
+    const double v = emb_value(lrow, k, part, Nc, Nt, Nm, dt, beta);
+    return Jrow ? v * Jrow[time_of(k < Nc ? k : k - Nc, Nt)] : v;
+  };
   double mx = 0.0;
-  for (int k = lane; k < N2; k += 32) mx = fmax(mx, fabs(emb_value(lrow, k, part, Nc, Nt, Nm, dt, beta)));
+  for (int k = lane; k < N2; k += 32) mx = fmax(mx, fabs(value(k)));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const double sc = pow2_scale(mx);
   if (lane == 0) sigma[row] = sc;
   const double fix_over_sc = ldexp(1.0, FIX) / sc;
   const size_t stride = (size_t)Nr * N2 * N2;
-  for (int k = lane; k < N2; k += 32)
-    write_slices(emb_value(lrow, k, part, Nc, Nt, Nm, dt, beta), fix_over_sc, as + row * N2 + k, stride);
+  for (int k = lane; k < N2; k += 32) write_digits_fast<S>(lambda_fixed(value(k), fix_over_sc), as + row * N2 + k, stride);
 }
 
-// one warp per (site i, vector column n): X = sum_j J_ij G_j (FP64), column scale, slices
+// one warp per (site i, vector column n): X = sum_j J_ij G_j (FP64), column scale, slices.
+// Warps walk the sites fastest for one column, so that the four reads of a neighbour's
+// column meet in L1 or L2 instead of coming from HBM four times.
+template <int NS>
 __global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restrict__ Jtab, const int* __restrict__ nbr,
-                           const int* __restrict__ nbond, int Nr, int Nt, int Nc, int ncol, int nslices,
+                           const int* __restrict__ nbond, int Nr, int Nt, int Nc, int ncol,
                            __nv_bfloat16* __restrict__ xs, double* __restrict__ tau) {
-  const size_t w = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const size_t wi = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
-  if (w >= (size_t)Nr * ncol) return;
-  const int i = (int)(w / ncol), n = (int)(w % ncol);
+  if (wi >= (size_t)Nr * ncol) return;
+  const int i = (int)(wi % Nr), n = (int)(wi / Nr);
+  const size_t w = (size_t)i * ncol + n;                   // slot of (i, n) in tau and in the slices
   const int N2 = 2 * Nc;
   int nb[4], bd[4];
 #pragma unroll
@@ -224,9 +238,70 @@ __global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restri
   for (int u = 0; u < PER_LANE; ++u) {
     const int z = lane + 32 * u;
     if (z < Nc) {
-      write_digits(scaled_to_fixed(x[u].x, FIX - e), dst + z, stride, nslices);
-      write_digits(scaled_to_fixed(x[u].y, FIX - e), dst + Nc + z, stride, nslices);
+      write_digits_fast<NS>(fixed_right(x[u].x, FIX - e), dst + z, stride);
+      write_digits_fast<NS>(fixed_right(x[u].y, FIX - e), dst + Nc + z, stride);
     }
+  }
+}
+
+// The same where every bond carries the same J(t): the factor sits in the Lambda slices
+// (k_oz_aprep with Jrow), and X = sum_j G_j is summed exactly as 2^-FIX fixed-point
+// integers, with no FP64 arithmetic.  The column scale is a power of two at least four
+// times the largest neighbour value, so the sum of four stays within it; one pass finds
+// it and a second (reading the same columns again, from L1 or L2) converts and sums.
+template <int NS>
+__global__ void k_oz_xprep_sum(const double2* __restrict__ G, const int* __restrict__ nbr, int Nr, int Nc, int ncol,
+                               __nv_bfloat16* __restrict__ xs, double* __restrict__ tau) {
+  const size_t wi = (size_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (wi >= (size_t)Nr * ncol) return;
+  const int i = (int)(wi % Nr), n = (int)(wi / Nr);
+  const size_t w = (size_t)i * ncol + n;
+  const int N2 = 2 * Nc;
+  const double2* col[4];
+  bool has[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int j = nbr[i * 4 + q];
+    has[q] = j >= 0;
+    col[q] = G + ((size_t)(has[q] ? j : i) * ncol + n) * Nc;
+  }
+  constexpr int PER_LANE = 256 / 32;
+  constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+  unsigned long long mb = 0;
+#pragma unroll
+  for (int u = 0; u < PER_LANE; ++u) {
+    const int z = lane + 32 * u;
+    if (z >= Nc) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!has[q]) continue;
+      const double2 g = col[q][z];
+      mb = max(mb, max((unsigned long long)__double_as_longlong(g.x) & ABS,
+                       (unsigned long long)__double_as_longlong(g.y) & ABS));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, mb, o));
+  // largest value < 2^(Emx - 1022), so 2^e with e = Emx - 1020 bounds four of them
+  const int Emx = (int)((mb >> 52) & 0x7FF);
+  const int e = Emx == 0 ? 0 : Emx - 1020;
+  if (lane == 0) tau[w] = __longlong_as_double((long long)(e + 1023) << 52);
+  const size_t stride = (size_t)Nr * ncol * N2;
+  __nv_bfloat16* dst = xs + w * N2;
+#pragma unroll
+  for (int u = 0; u < PER_LANE; ++u) {
+    const int z = lane + 32 * u;
+    if (z >= Nc) continue;
+    long long vr = 0, vi = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!has[q]) continue;
+      const double2 g = col[q][z];
+      vr += fixed_right(g.x, FIX - e);
+      vi += fixed_right(g.y, FIX - e);
+    }
+    write_digits_fast<NS>(vr, dst + z, stride);
+    write_digits_fast<NS>(vi, dst + Nc + z, stride);
   }
 }
 
@@ -527,7 +602,8 @@ int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, do
     if ((rc = grow(c, &st->aslices, &st->a_bytes, abytes, "Ozaki slices of Lambda"))) return rc;
     if (!st->sigma) DY_CUDA(c, cudaMalloc(&st->sigma, (size_t)Nr * N2 * sizeof(double)));
     size_t rows = (size_t)Nr * N2;
-    k_oz_aprep<<<(unsigned)((rows + 7) / 8), 256, 0, c->stream>>>(c->d_lam, Nr, c->Nt, c->Nm, c->dt, c->beta,
+    const double* Jrow = c->j_uniform && c->Nb > 0 ? c->dJ : nullptr;   // bond 0's row stands for all
+    k_oz_aprep<<<(unsigned)((rows + 7) / 8), 256, 0, c->stream>>>(c->d_lam, Jrow, Nr, c->Nt, c->Nm, c->dt, c->beta,
                                                                  st->aslices, st->sigma);
     c->launches += 1;
     if (!make_map4(&st->amap, st->aslices, N2, N2, Nr, S, BM))
@@ -551,9 +627,20 @@ int oz_residual(dyson_ctx* c, int ncol, int gs, const double2* G, float* r32, do
     st->smem_set = true;
   }
   size_t warps = (size_t)Nr * ncol;
-  k_oz_xprep<<<(unsigned)((warps + 7) / 8), 256, 0, c->stream>>>(G, c->dJ, c->d_nbr, c->d_nbond, Nr, c->Nt, Nc,
-                                                                ncol, short_split ? S_SHORT : S, st->xslices,
-                                                                st->tau);
+  const unsigned xblocks = (unsigned)((warps + 7) / 8);
+  if (c->j_uniform && c->Nb > 0) {
+    if (short_split)
+      k_oz_xprep_sum<S_SHORT><<<xblocks, 256, 0, c->stream>>>(G, c->d_nbr, Nr, Nc, ncol, st->xslices, st->tau);
+    else
+      k_oz_xprep_sum<S><<<xblocks, 256, 0, c->stream>>>(G, c->d_nbr, Nr, Nc, ncol, st->xslices, st->tau);
+  } else {
+    if (short_split)
+      k_oz_xprep<S_SHORT><<<xblocks, 256, 0, c->stream>>>(G, c->dJ, c->d_nbr, c->d_nbond, Nr, c->Nt, Nc, ncol,
+                                                           st->xslices, st->tau);
+    else
+      k_oz_xprep<S><<<xblocks, 256, 0, c->stream>>>(G, c->dJ, c->d_nbr, c->d_nbond, Nr, c->Nt, Nc, ncol,
+                                                     st->xslices, st->tau);
+  }
   const long long tiles = (long long)(N2 / BM) * ((ncol + BN - 1) / BN) * Nr;
   const int grid = (int)std::min<long long>(tiles, st->num_sms);
   if (short_split)

@@ -106,12 +106,35 @@ def test_tensor_core_path_matches_dense(torch_cuda, lib, kw):
         assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
 
 
+@pytest.mark.parametrize("kw", TC_CASES[:2])
+def test_uniform_hopping_residual_matches_dense(torch_cuda, lib, kw):
+    """Hopping equal on every bond (the trapped and driven lattices): the residual folds J(t)
+    into the Lambda slices and sums the neighbours' columns as exact fixed-point integers,
+    with no FP64 gather. The refined result must meet the dense solve at 1e-12 all the same
+    (seven slices at this tolerance)."""
+    p = wl.small(**kw)
+    assert np.all(p.J == p.J[:1])                            # one J(t) row for every bond
+    S = dyson.setup(p)
+    sources = list(range(p.Nr))
+    ref = dyson.dense_solve(S, dyson.rhs_block_columns(S, sources))
+    s = _solver(p)
+    s.profile(True)
+    got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-13)
+    assert s.profile_query(4)[0] == res.report["refinements"] > 0
+    for q in range(len(sources)):
+        assert _rel(got[q], ref[:, :, q * p.Nc:(q + 1) * p.Nc]) < 1e-12
+
+
+@pytest.mark.parametrize("tables", ["per_bond", "uniform"])
 @pytest.mark.parametrize("tol", [1e-8, 1e-6])
-def test_short_slice_residual_at_loose_tolerances(torch_cuda, lib, tol):
+def test_short_slice_residual_at_loose_tolerances(torch_cuda, lib, tol, tables):
     """Tolerances of 1e-8 and looser compute the FP64-accurate residual from the first five
     operand slices (15 products): the residual the solve reports must still be the true
-    residual of the returned G, re-evaluated in complex128 by the oracle, to 2 % of the tolerance."""
-    p = wl.random_tables(wl.small(**TC_CASES[0]), seed=31, rel=0.2)
+    residual of the returned G, re-evaluated in complex128 by the oracle, to 2 % of the tolerance.
+    Per-bond hopping gathers X in FP64; uniform hopping sums it in fixed point."""
+    p = wl.small(**TC_CASES[0])
+    if tables == "per_bond":
+        p = wl.random_tables(p, seed=31, rel=0.2)
     S = dyson.setup(p)
     sources = list(range(p.Nr))
     s = _solver(p)
