@@ -60,6 +60,8 @@ def parse():
                     help="block columns of the driven 32x32 (Nc = 384) leg, streamed in tuned chunks (0 skips it)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the 24x24 adjoint leg")
     ap.add_argument("--no-selfenergy", action="store_true", help="skip the self-consistency loop leg")
+    ap.add_argument("--graph-sweeps", type=int, default=16,
+                    help="sweeps per captured graph of the inner series (0: one host synchronisation per sweep)")
     ap.add_argument("--sweep-variant", default="auto",
                     choices=["auto", "single_cta", "cta_pair", "fused_pair", "fused_pair_wide"],
                     help="override the autotuner's sweep variant (profiling runs: kernel timings under a "
@@ -568,6 +570,7 @@ def run_gb300(args, rank, world, local):
     stream = torch.cuda.Stream(device=dev)
     mm = measure_matmul_peaks(dev)
     solver = binding.Solver(p, device=local, stream=stream)
+    solver.set_graph_sweeps(args.graph_sweeps)
     PREC = binding.PREC_TF32X3_F64REF
 
     def step(k, s=solver):
@@ -612,6 +615,7 @@ def run_gb300(args, rank, world, local):
     flops = sum(r["gemm_flops"] for r in reports)
     tflops_local = flops / (elapsed_ms * 1e-3) / 1e12
     sweeps = [r["sweeps"] for r in reports]
+    host_syncs = [r["host_syncs"] for r in reports]
     refinements = [r["refinements"] for r in reports]
     residual = max(r["residual"] for r in reports)
 
@@ -672,6 +676,7 @@ def run_gb300(args, rank, world, local):
             s2 = binding.Solver(p, device=local, stream=stream)
             s2.set_sweep_variant(tuning["sweep_variant"])
             s2.set_chunk(tuning["chunk_block_columns"])
+            s2.set_graph_sweeps(args.graph_sweeps)
             s2.build_sigma()
             # the same source batches as the timed device steps
             s2.solve(dist.step_sources(p.Nr, args.batch, rank, world, args.warmup + k), precision=PREC,
@@ -723,6 +728,7 @@ def run_gb300(args, rank, world, local):
                                          round(c["vector_columns_per_s"])) for c in tuning["candidates"]]},
             "contour_gemm_tflops": tflops_local * world, "vector_columns_per_s": value * Nc,
             "sweeps_per_step": sweeps, "refinements_per_step": refinements, "max_rel_residual": residual,
+            "host_syncs_per_step": host_syncs, "graph_sweeps": args.graph_sweeps,
             "clocks": clk, "gpu_launches": gpu_launches, "roofline": roof}
     line.update(extras)
     # the verification summary closes the line (compact, rounded), so that a kept tail of

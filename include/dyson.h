@@ -109,7 +109,8 @@ typedef struct {
   int64_t kernel_launches;      /* CUDA kernels this call launched                         */
   int32_t inner_gmres;          /* 1 if a refinement used the GMRES inner solver (its      */
                                 /* matvecs are counted in sweeps), else 0                  */
-  int32_t reserved;
+  int32_t host_syncs;           /* times the call waited for the device (norm and error     */
+                                /* reads; one per graph replay of the inner series)         */
 } dyson_report;
 
 /* Create a context on `device`, ordering work on `cuda_stream` (a cudaStream_t,
@@ -347,6 +348,17 @@ int dyson_set_sweep_variant(dyson_ctx* ctx, int variant);
  * paper has no counterpart: the call exists so that tests can make a healthy pipeline
  * run out of time and check that path.  INVALID_ARG for a limit outside [0, 60]. */
 int dyson_set_wait_limit(dyson_ctx* ctx, double seconds);
+
+/* Sweeps per captured CUDA graph of the inner series (App. C) on the fused tensor-core
+ * sweep: the series runs from replays of a graph of `sweeps` sweeps, each followed by a
+ * one-warp kernel that applies the series' stopping rule on the device and lets the
+ * remaining sweeps of a replay return at once (the replayed sweeps take their sweep
+ * number for support truncation from the device).  One host synchronisation per replay
+ * instead of one per sweep; results and sweep counts are the same as with 0, which keeps
+ * one synchronisation per sweep.  The graph is captured on a private stream and launched
+ * on the context's stream; not used while that stream is being captured by the caller.
+ * Default 16; INVALID_ARG unless even and in 0..64. */
+int dyson_set_graph_sweeps(dyson_ctx* ctx, int sweeps);
 
 /* Point-group symmetry of the problem (App. A).  DYSON_SYMMETRY_C4V: on a
  * square lattice with the centred trap and drive tables invariant under the

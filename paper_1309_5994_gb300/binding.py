@@ -61,7 +61,7 @@ class Report(C.Structure):
     _fields_ = [("sweeps", C.c_int32), ("refinements", C.c_int32), ("chunks", C.c_int32),
                 ("status", C.c_int32), ("update", C.c_double), ("residual", C.c_double),
                 ("gemm_flops", C.c_double), ("seconds", C.c_double), ("kernel_launches", C.c_int64),
-                ("inner_gmres", C.c_int32), ("reserved", C.c_int32)]
+                ("inner_gmres", C.c_int32), ("host_syncs", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -72,7 +72,7 @@ EXPORTS = ["dyson_init", "dyson_build_sigma", "dyson_copy_sigma", "dyson_solve_c
            "dyson_profile", "dyson_profile_query", "dyson_set_chunk",
            "dyson_launch_count", "dyson_destroy", "dyson_last_error", "dyson_version",
            "dyson_solve_block_column_noalloc", "dyson_noalloc_last_error", "dyson_set_sweep_variant",
-           "dyson_set_wait_limit",
+           "dyson_set_wait_limit", "dyson_set_graph_sweeps",
            "dyson_batch_create", "dyson_batch_solve", "dyson_batch_launch_count", "dyson_batch_last_error",
            "dyson_batch_destroy", "dyson_set_inner_solver", "dyson_autotune", "dyson_set_symmetry",
            "dyson_adjoint_obs", "dyson_extrapolate_dt", "dyson_set_support_truncation", "dyson_local_greens",
@@ -110,6 +110,7 @@ def load(path: str = _LIB_PATH):
     lib.dyson_set_chunk.argtypes = [P, C.c_int32]
     lib.dyson_set_sweep_variant.argtypes = [P, C.c_int]
     lib.dyson_set_wait_limit.argtypes = [P, C.c_double]
+    lib.dyson_set_graph_sweeps.argtypes = [P, C.c_int]
     lib.dyson_set_inner_solver.argtypes = [P, C.c_int, C.c_int32]
     lib.dyson_autotune.argtypes = [P, C.c_int32, C.POINTER(Tuning)]
     lib.dyson_set_symmetry.argtypes = [P, C.c_int]
@@ -374,6 +375,10 @@ class Solver:
     def set_wait_limit(self, seconds: float):
         """Time limit of the tensor-core pipelines' bounded waits on this device (0: the default 2 s)."""
         self._check(self.lib.dyson_set_wait_limit(self.h, float(seconds)))
+
+    def set_graph_sweeps(self, sweeps: int):
+        """Sweeps per captured graph of the inner series (0: one synchronisation per sweep)."""
+        self._check(self.lib.dyson_set_graph_sweeps(self.h, int(sweeps)))
 
     def set_sweep_variant(self, variant: int):
         self._check(self.lib.dyson_set_sweep_variant(self.h, variant))

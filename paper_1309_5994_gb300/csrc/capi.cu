@@ -99,6 +99,7 @@ int read_norms(dyson_ctx* c, int ng, bool with_scale) {
   DY_CUDA(c, cudaMemcpyAsync(c->h_norm, c->d_norm, (with_scale ? 2 : 1) * (size_t)ng * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, c->stream));
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->host_syncs += 1;
   flush_timers(c);
   return DYSON_OK;
 }
@@ -163,6 +164,74 @@ int solve_f64(dyson_ctx* c, int ncol, int gs, double tol, int max_sweeps, double
   return status;
 }
 
+// Stopping state of the inner series, the same fields the host loop of inner_solve keeps;
+// on the device for sweeps replayed from a captured graph.
+struct SeriesState {
+  double best, peak, last;
+  double hist[kStallSweeps];           // the last kStallSweeps updates (ring)
+  int since_best, since_peak, sweeps;
+  int run;                             // 1 while the series goes on (read by the fused sweep)
+  int outcome;
+};
+enum { SERIES_RUNNING = 0, SERIES_STOPPED, SERIES_EXHAUSTED, SERIES_ABORTED, SERIES_NOT_FINITE };
+
+// After one sweep of a captured series: the update max_q norm_q / rref_q (norm words
+// cleared for the next sweep) and the stopping rule of inner_solve's host loop, in the
+// same order.  One warp; returns at once once the series has stopped.
+__global__ void k_series_check(unsigned long long* __restrict__ norm, const double* __restrict__ rref, int ng,
+                               int max_sweeps, double target, double abort_peak, SeriesState* __restrict__ S) {
+  if (!S->run) return;
+  double m = 0.0;
+  int bad = 0;
+  for (int q = threadIdx.x; q < ng; q += 32) {
+    const double v = __longlong_as_double((long long)norm[q]) / fmax(rref[q], 1e-300);
+    if (!(v == v)) bad = 1;
+    else m = fmax(m, v);
+    norm[q] = 0ull;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (threadIdx.x != 0) return;
+  const double upd = bad ? __longlong_as_double(0x7ff0000000000000ll) : m;
+  const int sweep = ++S->sweeps;
+  S->last = upd;
+  if (!(upd < kDivergedGrowth)) {
+    S->outcome = SERIES_NOT_FINITE;
+    S->run = 0;
+    return;
+  }
+  if (upd > S->peak) {
+    S->peak = upd;
+    S->best = upd;
+    S->since_best = 0;
+    S->since_peak = 0;
+  } else {
+    ++S->since_peak;
+    if (upd < S->best) {
+      S->best = upd;
+      S->since_best = 0;
+    } else {
+      ++S->since_best;
+    }
+  }
+  const double ago = S->hist[sweep % kStallSweeps];
+  S->hist[sweep % kStallSweeps] = upd;
+  int out = SERIES_RUNNING;
+  if (S->peak > abort_peak) out = SERIES_ABORTED;
+  else if ((upd <= target && (upd < S->peak || upd == 0.0)) ||
+           (S->since_best >= kStallSweeps && S->best < kStallDrop * S->peak) ||
+           (S->since_peak >= kStallSweeps && upd < kStallDrop * S->peak && upd > kFlatRatio * ago))
+    out = SERIES_STOPPED;
+  else if (sweep >= max_sweeps)
+    out = SERIES_EXHAUSTED;
+  if (out != SERIES_RUNNING) {
+    S->outcome = out;
+    S->run = 0;
+  }
+}
+
 // one 3xTF32 tensor-core sweep dout = r + K din with per-kind event timing: the
 // fused gather + GEMM launch, or the gather launch and the GEMM launch
 int tc_timed_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* din, float* dout, const int* act,
@@ -184,6 +253,10 @@ int tc_timed_sweep(dyson_ctx* c, int ncol, int gs, const float* r, const float* 
 // act (optional): support truncation of the tensor-core sweeps (tc_sweep), valid
 // while every column of r32 is zero off its source site
 // r_on_sources: r32 is non-zero only on each column's source site (the first right-hand side)
+// With the fused sweep the series runs from replays of a captured graph of
+// c->graph_sweeps sweeps, each followed by k_series_check: one host synchronisation per
+// replay instead of one per sweep.  The replayed sweeps take their sweep number (for the
+// support table) from the device count of sweeps done.
 int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float* da, float* db, int max_sweeps,
                 const std::vector<double>& rref, float** dres, dyson_report* rep, double* peak_out,
                 double abort_peak = std::numeric_limits<double>::infinity(), const int* act = nullptr,
@@ -193,15 +266,22 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
   const size_t n32 = (size_t)c->Nr * ncol * 2 * c->Nc;
   DY_CUDA(c, cudaMemcpyAsync(da, r32, n32 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
   if (act) DY_CUDA(c, cudaMemsetAsync(db, 0, n32 * sizeof(float), c->stream));   // skipped tiles stay 0
-  double best = std::numeric_limits<double>::infinity(), peak = 0.0;
-  double hist[kStallSweeps] = {};                      // the last kStallSweeps updates (ring)
-  int since_best = 0, since_peak = 0, rc;
-  for (int sweep = 1; sweep <= max_sweeps; ++sweep) {
+  const int rform = r_on_sources ? TC_R_ON_SOURCES : TC_R_DENSE;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  // (not inside a caller's own capture of the stream)
+  const bool graph = c->graph_sweeps > 0 && precision == DYSON_PREC_TF32X3_F64REF && c->use_tc &&
+                     tc_uses_fused(c) && cudaStreamIsCapturing(c->stream, &cap) == cudaSuccess &&
+                     cap == cudaStreamCaptureStatusNone;
+  const int eager_until = graph ? 0 : max_sweeps;
+  SeriesState S = {};
+  S.best = std::numeric_limits<double>::infinity();
+  S.run = 1;
+  int rc;
+  while (S.run && S.sweeps < std::min(max_sweeps, eager_until)) {
+    const int sweep = S.sweeps + 1;
     DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
     if (precision == DYSON_PREC_TF32X3_F64REF && c->use_tc) {
-      if ((rc = tc_timed_sweep(c, ncol, gs, r32, da, db, act, sweep,
-                               r_on_sources ? TC_R_ON_SOURCES : TC_R_DENSE)))
-        return rc;
+      if ((rc = tc_timed_sweep(c, ncol, gs, r32, da, db, act, sweep, rform))) return rc;
     } else {
       KernelTimer t(c, DYSON_KERNEL_SWEEP_F32);
       launch_sweep_f32_simt(c->d_lam32, c->d_Jz, c->d_nbr, c->d_nbond, r32, da, db, c->Nr, c->Nc, ncol, gs,
@@ -214,40 +294,147 @@ int inner_solve(dyson_ctx* c, int ncol, int gs, int precision, float* r32, float
     if ((rc = read_norms(c, ng, false))) return rc;
     if (c->use_tc && (rc = tc_error_status(c))) return rc;
     std::swap(da, db);
-    double upd = rel_max(c->h_norm, rref.data(), ng);
+    const double upd = rel_max(c->h_norm, rref.data(), ng);
+    S.sweeps = sweep;
+    S.last = upd;
     rep->sweeps += 1;
     rep->gemm_flops += sweep_flops(c, ncol);
     rep->update = upd;
     if (!(upd < kDivergedGrowth)) return ctx_fail(c, DYSON_ERR_DIVERGED, "FP32 series update not finite");
     // stopping rule of the inner series (detail.cuh); the stall is judged only on
-    // the decay after the latest peak
-    if (upd > peak) {
-      peak = upd;
-      best = upd;
-      since_best = 0;
-      since_peak = 0;
+    // the decay after the latest peak (k_series_check applies the same, in this order)
+    if (upd > S.peak) {
+      S.peak = upd;
+      S.best = upd;
+      S.since_best = 0;
+      S.since_peak = 0;
     } else {
-      ++since_peak;
-      if (upd < best) {
-        best = upd;
-        since_best = 0;
+      ++S.since_peak;
+      if (upd < S.best) {
+        S.best = upd;
+        S.since_best = 0;
       } else {
-        ++since_best;
+        ++S.since_best;
       }
     }
-    const double ago = hist[sweep % kStallSweeps];       // the update kStallSweeps sweeps ago
-    hist[sweep % kStallSweeps] = upd;
-    if (peak > abort_peak) {
-      if (peak_out) *peak_out = peak;
+    const double ago = S.hist[sweep % kStallSweeps];     // the update kStallSweeps sweeps ago
+    S.hist[sweep % kStallSweeps] = upd;
+    if (S.peak > abort_peak) {
+      if (peak_out) *peak_out = S.peak;
       return DYSON_ERR_DIVERGED;                           // the caller switches to GMRES
     }
-    if (upd <= target && (upd < peak || upd == 0.0)) break;   // on the decay, not before the peak
-    if (since_best >= kStallSweeps && best < kStallDrop * peak) break;
-    if (since_peak >= kStallSweeps && upd < kStallDrop * peak && upd > kFlatRatio * ago) break;
-    if (sweep == max_sweeps && exhausted) *exhausted = true;
+    if ((upd <= target && (upd < S.peak || upd == 0.0)) ||  // on the decay, not before the peak
+        (S.since_best >= kStallSweeps && S.best < kStallDrop * S.peak) ||
+        (S.since_peak >= kStallSweeps && upd < kStallDrop * S.peak && upd > kFlatRatio * ago)) {
+      S.run = 0;
+      S.outcome = SERIES_STOPPED;
+    } else if (sweep == max_sweeps) {
+      S.run = 0;
+      S.outcome = SERIES_EXHAUSTED;
+    }
   }
+  if (S.run && graph) {
+    // the rest of the series from a captured graph of S_g sweeps (even, so that every
+    // replay starts from da), each followed by its check
+    const int Sg = c->graph_sweeps;
+    if (!c->d_series) {
+      DY_CUDA(c, cudaMalloc(&c->d_series, sizeof(SeriesState)));
+      DY_CUDA(c, cudaMallocHost(&c->h_series, sizeof(SeriesState)));
+    }
+    if (c->rref_cap < ng) {
+      if (c->d_rref) cudaFree(c->d_rref);
+      c->d_rref = nullptr;
+      c->rref_cap = 0;
+      DY_CUDA(c, cudaMalloc(&c->d_rref, (size_t)ng * sizeof(double)));
+      c->rref_cap = ng;
+    }
+    SeriesState* hS = static_cast<SeriesState*>(c->h_series);
+    SeriesState* dS = static_cast<SeriesState*>(c->d_series);
+    *hS = S;
+    if ((rc = tc_prepare_sweep(c, ncol))) return rc;     // nothing to allocate or encode while capturing
+    DY_CUDA(c, cudaMemcpyAsync(c->d_rref, rref.data(), (size_t)ng * sizeof(double), cudaMemcpyHostToDevice,
+                               c->stream));                // pageable: complete when the call returns
+    DY_CUDA(c, cudaMemcpyAsync(dS, hS, sizeof(SeriesState), cudaMemcpyHostToDevice, c->stream));
+    DY_CUDA(c, cudaMemsetAsync(c->d_norm, 0, (size_t)ng * sizeof(unsigned long long), c->stream));
+    const int64_t launches0 = c->launches;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    // captured on a private stream (any stream of the caller's, the default one included,
+    // can then launch it); the context's launches go there while capturing
+    if (!c->cap_stream) DY_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = c->stream;
+    DY_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->cap_stream;
+    c->sweep_run = &dS->run;
+    c->sweep_count = &dS->sweeps;
+    int cap_rc = DYSON_OK;
+    for (int k = 0; k < Sg && cap_rc == DYSON_OK; ++k) {
+      cap_rc = tc_sweep(c, ncol, gs, r32, k % 2 ? db : da, k % 2 ? da : db, TC_GATHER | TC_GEMM, act, 0, rform);
+      if (cap_rc == DYSON_OK)
+        k_series_check<<<1, 32, 0, c->stream>>>(c->d_norm, c->d_rref, ng, max_sweeps, target, abort_peak, dS);
+    }
+    c->sweep_run = nullptr;
+    c->sweep_count = nullptr;
+    c->stream = user;
+    cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+    if (cap_rc) {
+      if (g) cudaGraphDestroy(g);
+      return cap_rc;
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return ctx_fail(c, DYSON_ERR_CUDA, std::string("inner series graph: ") + cudaGetErrorString(ce));
+    c->launches = launches0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+    }
+    rc = DYSON_OK;
+    while (rc == DYSON_OK) {
+      const int before = hS->sweeps;
+      if (e0) cudaEventRecord(e0, c->stream);
+      cudaError_t le = cudaGraphLaunch(ge, c->stream);
+      if (e1) cudaEventRecord(e1, c->stream);
+      if (le == cudaSuccess && c->use_tc) rc = tc_error_enqueue(c);
+      if (le == cudaSuccess && rc == DYSON_OK)
+        le = cudaMemcpyAsync(hS, dS, sizeof(SeriesState), cudaMemcpyDeviceToHost, c->stream);
+      if (le == cudaSuccess && rc == DYSON_OK) le = cudaStreamSynchronize(c->stream);
+      if (le != cudaSuccess) {
+        rc = ctx_fail(c, DYSON_ERR_CUDA, std::string("inner series graph: ") + cudaGetErrorString(le));
+        break;
+      }
+      c->host_syncs += 1;
+      if (rc || (c->use_tc && (rc = tc_error_status(c)))) break;
+      const int n_run = hS->sweeps - before;
+      c->launches += 2 * Sg;
+      rep->sweeps += n_run;
+      rep->gemm_flops += n_run * sweep_flops(c, ncol);
+      rep->update = hS->last;
+      float ms = 0.f;
+      if (e0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        c->prof_ms[DYSON_KERNEL_SWEEP_TC_FUSED] += ms;     // the replay, its checks included
+        c->prof_launches[DYSON_KERNEL_SWEEP_TC_FUSED] += n_run;
+      }
+      if (!hS->run) {
+        if (n_run % 2) std::swap(da, db);                  // the last sweep wrote db
+        break;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaGraphExecDestroy(ge);
+    if (rc) return rc;
+    S = *hS;
+    if (S.outcome == SERIES_NOT_FINITE) return ctx_fail(c, DYSON_ERR_DIVERGED, "FP32 series update not finite");
+    if (S.outcome == SERIES_ABORTED) {
+      if (peak_out) *peak_out = S.peak;
+      return DYSON_ERR_DIVERGED;
+    }
+  }
+  if (S.outcome == SERIES_EXHAUSTED && exhausted) *exhausted = true;
   *dres = da;
-  if (peak_out) *peak_out = peak;
+  if (peak_out) *peak_out = S.peak;
   return DYSON_OK;
 }
 
@@ -389,8 +576,9 @@ int solve_mixed(dyson_ctx* c, int ncol, int gs, int precision, double tol, int m
       c->launches += 1;
     }
     DY_CUDA(c, cudaGetLastError());
+    if (c->use_oz && (rc = oz_error_enqueue(c))) return rc;   // read with the norms: one synchronisation
     if ((rc = read_norms(c, ng, false))) return rc;
-    if (c->use_oz && (rc = oz_check_error(c))) return rc;
+    if (c->use_oz && (rc = oz_error_status(c))) return rc;
     rep->refinements += 1;
     rep->gemm_flops += sweep_flops(c, ncol);
     double res = rel_max(c->h_norm, scale.data(), ng);
@@ -618,15 +806,16 @@ struct ReportScope {
   dyson_ctx* c;
   dyson_report rep;
   dyson_report* out;
-  int64_t launches0;
+  int64_t launches0, syncs0;
   std::chrono::steady_clock::time_point t0;
-  ReportScope(dyson_ctx* cc, dyson_report* o) : c(cc), out(o), launches0(cc->launches) {
+  ReportScope(dyson_ctx* cc, dyson_report* o) : c(cc), out(o), launches0(cc->launches), syncs0(cc->host_syncs) {
     std::memset(&rep, 0, sizeof rep);
     t0 = std::chrono::steady_clock::now();
   }
   int finish(int code) {
     rep.status = code;
     rep.kernel_launches = c->launches - launches0;
+    rep.host_syncs = (int32_t)(c->host_syncs - syncs0);
     rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (out) *out = rep;
     return code;
@@ -963,6 +1152,13 @@ int dyson_set_wait_limit(dyson_ctx* c, double seconds) {
   return oz_set_wait_limit(c, ns);
 }
 
+int dyson_set_graph_sweeps(dyson_ctx* c, int sweeps) {
+  if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
+  if (sweeps < 0 || sweeps > 64 || sweeps % 2) return ctx_fail(c, DYSON_ERR_INVALID_ARG, "sweeps must be even, 0..64");
+  c->graph_sweeps = sweeps;
+  return DYSON_OK;
+}
+
 int dyson_set_sweep_variant(dyson_ctx* c, int variant) {
   if (!c) return fail_noctx(DYSON_ERR_INVALID_ARG, "NULL context");
   if (variant < DYSON_SWEEP_SINGLE_CTA || variant > DYSON_SWEEP_FUSED_PAIR_WIDE)
@@ -983,10 +1179,12 @@ void dyson_destroy(dyson_ctx* c) {
   if (c->d_sym_perm) cudaFree(c->d_sym_perm);
   void* ptrs[] = {c->dU, c->dJ, c->d_nbr, c->d_nbond, c->d_eps, c->d_phase, c->d_lam, c->d_JW, c->d_Jz,
                   c->d_lam32, c->d_lam_hi, c->d_lam_lo, c->d_obs, c->work, c->d_src_site, c->d_src_time,
-                  c->d_norm, c->adj, c->d_act};
+                  c->d_norm, c->adj, c->d_act, c->d_series, c->d_rref};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->h_norm) cudaFreeHost(c->h_norm);
+  if (c->h_series) cudaFreeHost(c->h_series);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 

@@ -100,6 +100,16 @@ struct dyson_ctx {
   double dt = 0, beta = 0, curvature = 0, mu = 0;
   std::vector<double> U, J;          // host copies of the drive tables
   bool j_uniform = false;            // every bond carries the same J(t) row
+  // inner series under captured graphs: sweeps per graph (0: one host synchronisation per
+  // sweep); while a graph is captured, the flag its fused sweeps read (0: the series stopped)
+  int graph_sweeps = 16;
+  const int* sweep_run = nullptr;
+  const int* sweep_count = nullptr;  // while capturing: the device count of sweeps done
+  cudaStream_t cap_stream = nullptr; // private stream the series graph is captured on (lazy)
+  void* d_series = nullptr;          // device stopping state of the captured series
+  void* h_series = nullptr;          // pinned mirror
+  double* d_rref = nullptr;          // reference norms of the current inner solve
+  int rref_cap = 0;
 
   // device tables
   double* dU = nullptr;              // [Nr][Nt]
@@ -137,6 +147,7 @@ struct dyson_ctx {
   int max_refinements = 12;
   int chunk_override = 0;
   int64_t launches = 0;              // kernels launched by this context since dyson_init
+  int64_t host_syncs = 0;            // host waits for the device in solves (reported per call)
 
   // optional per-launch event timing
   struct Pending {

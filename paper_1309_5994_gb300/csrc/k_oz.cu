@@ -73,6 +73,7 @@ struct OzState {
   const void* xmap_ptr = nullptr;
   int xmap_ncol = -1;
   int* d_err = nullptr;
+  int* h_err = nullptr;               // pinned mirror of d_err
   int num_sms = 1;
   bool smem_set = false;
 };
@@ -662,17 +663,31 @@ int oz_set_wait_limit(dyson_ctx* c, unsigned long long ns) {
   return DYSON_OK;
 }
 
+int oz_error_enqueue(dyson_ctx* c) {
+  OzState* st = static_cast<OzState*>(c->oz);
+  if (!st || !st->d_err) return DYSON_OK;
+  if (!st->h_err) DY_CUDA(c, cudaMallocHost(&st->h_err, sizeof(int)));
+  *st->h_err = 0;
+  DY_CUDA(c, cudaMemcpyAsync(st->h_err, st->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  return DYSON_OK;
+}
+
+int oz_error_status(dyson_ctx* c) {
+  OzState* st = static_cast<OzState*>(c->oz);
+  if (!st || !st->h_err || !*st->h_err) return DYSON_OK;
+  *st->h_err = 0;
+  cudaMemsetAsync(st->d_err, 0, sizeof(int), c->stream);
+  return ctx_fail(c, DYSON_ERR_TIMEOUT, "a residual pipeline wait exceeded its time limit");
+}
+
 int oz_check_error(dyson_ctx* c) {
   OzState* st = static_cast<OzState*>(c->oz);
   if (!st || !st->d_err) return DYSON_OK;
-  int h = 0;
-  DY_CUDA(c, cudaMemcpyAsync(&h, st->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int rc = oz_error_enqueue(c);
+  if (rc) return rc;
   DY_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (h) {
-    cudaMemsetAsync(st->d_err, 0, sizeof(int), c->stream);
-    return ctx_fail(c, DYSON_ERR_TIMEOUT, "a residual pipeline wait exceeded its time limit");
-  }
-  return DYSON_OK;
+  c->host_syncs += 1;
+  return oz_error_status(c);
 }
 
 void oz_release(dyson_ctx* c) {
@@ -681,6 +696,7 @@ void oz_release(dyson_ctx* c) {
   void* ptrs[] = {st->aslices, st->sigma, st->xslices, st->tau, st->d_err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (st->h_err) cudaFreeHost(st->h_err);
   delete st;
   c->oz = nullptr;
 }

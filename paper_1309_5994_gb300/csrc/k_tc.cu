@@ -761,9 +761,15 @@ __global__ void __launch_bounds__(F_THREADS, 1)
                const int* __restrict__ rsrc, const float* __restrict__ Jz, const int* __restrict__ nbr,
                const int* __restrict__ nbond, int Lx,
                int Ly, int Nc, int ncol, int gs, unsigned long long* __restrict__ norm, int* __restrict__ err,
-               const int* __restrict__ act, int sweep) {
+               const int* __restrict__ act, int sweep, const int* __restrict__ run,
+               const int* __restrict__ sweeps_done) {
   using namespace ptx;
   using Cfg = FusedCfg<GT>;
+  // a sweep of a captured graph after the series has stopped: nothing to do (every CTA
+  // reads the same flag, before any barrier, cluster or TMEM step); in a captured graph
+  // the sweep number (for the support table) is the device count of sweeps done, plus one
+  if (run && *run == 0) return;
+  if (sweeps_done) sweep = *sweeps_done + 1;
   constexpr int STAGES = Cfg::STAGES, NBUF = Cfg::NBUF, STAGE = Cfg::STAGE;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1237,13 +1243,15 @@ int launch_fused(dyson_ctx* c, int ncol, int gs, const float* r, const float* di
   DY_CUDA(c, cudaLaunchKernelEx(&cfg, k_tc_fused<GT>, st->a_hi, st->a_lo, r, din, dout, rsrc,
                                 (const float*)c->d_Jz,
                                 (const int*)c->d_nbr, (const int*)c->d_nbond, c->Lx, c->Ly, c->Nc, ncol, gs,
-                                c->d_norm, st->d_err, act, sweep));
+                                c->d_norm, st->d_err, act, sweep, c->sweep_run, c->sweep_count));
   DY_CUDA(c, cudaGetLastError());
   c->launches += 1;
   return DYSON_OK;
 }
 
 }  // namespace
+
+int tc_prepare_sweep(dyson_ctx* c, int ncol) { return tc_prepare(c, ncol, fused_gt(c) == 0); }
 
 int tc_fill_instance(dyson_ctx* c, int ncol, int gs, const float* r, float* buf0, float* buf1,
                      unsigned long long* norm, const int* active, TcInst* e, CUtensorMap* a_hi, CUtensorMap* a_lo,

@@ -40,6 +40,8 @@ bool tc_uses_pair(dyson_ctx* c);
 // the context's variant is DYSON_SWEEP_FUSED_PAIR (Nc % 128 == 0) or
 // DYSON_SWEEP_FUSED_PAIR_WIDE (Nc % 256 == 0); TC_GATHER alone then launches nothing
 bool tc_uses_fused(dyson_ctx* c);
+// tensor maps and buffers of tc_sweep for ncol columns, set up ahead of a stream capture
+int tc_prepare_sweep(dyson_ctx* c, int ncol);
 // one sweep d_out = r + K d_in over the FP32 planar chunk state of ncol vector columns;
 // writes c->d_norm[q] for groups of gs columns (gs a multiple of 32, Nc a multiple of 64).
 // phases: TC_GATHER launches X = J d_in, TC_GEMM launches the tensor-core product and

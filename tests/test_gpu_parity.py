@@ -199,6 +199,33 @@ def test_fused_sweep_matches_dense(torch_cuda, lib, kw, sources, variant):
         assert np.abs(n[src] - n_ref).max() < 1e-11 and np.abs(e[src] - e_ref).max() < 1e-11
 
 
+@pytest.mark.parametrize("kw,sources,variant", FUSED_CASES[:2] + [(FUSED_CASES[1][0], list(range(12)), 2)])
+def test_graph_replayed_series_is_bit_identical(torch_cuda, lib, kw, sources, variant):
+    """The inner series replayed from captured graphs (its stopping rule applied on the
+    device, one host synchronisation per graph of sweeps) returns the same G bit for bit,
+    the same sweep and refinement counts and the same residual as the loop with one
+    synchronisation per sweep: after truncated first sweeps (a few sources) and without
+    them (every site a source), and with a graph of 2 sweeps, where the series stops
+    inside a replay."""
+    p = wl.random_tables(wl.small(**kw), seed=23, rel=0.2)
+    out = {}
+    for gsw in (0, 16, 2):
+        s = _solver(p)
+        s.set_sweep_variant(variant)
+        s.set_graph_sweeps(gsw)
+        got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-10)
+        out[gsw] = (got, res.report["sweeps"], res.report["refinements"], res.report["residual"])
+        if gsw == 16:
+            from paper_1309_5994_gb300 import binding
+            for bad in (3, -2, 66):
+                with pytest.raises(binding.DysonError):
+                    s.set_graph_sweeps(bad)
+        s.close()
+    for gsw in (16, 2):
+        assert np.array_equal(out[gsw][0], out[0][0])
+        assert out[gsw][1:] == out[0][1:]
+
+
 @pytest.mark.parametrize("case", ["nc64_ragged", "nc256_pair", "nc256_fused"])
 def test_support_truncation_is_bit_identical(torch_cuda, lib, case):
     """Skipping the (site, column-tile) blocks the first series has not reached yet
