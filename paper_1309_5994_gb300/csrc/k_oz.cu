@@ -19,8 +19,9 @@
 // column scale, the Lambda slices are the first five of seven; truncation ~2^-35 of
 // |A||X|, two orders below such a tolerance).
 //
-// Kernels: k_oz_aprep (once per Lambda), k_oz_xprep (gather + scale + slice of X
-// per residual), k_oz_gemm (persistent: TMA + tcgen05.mma kind::f16 into two
+// Kernels: k_oz_aprep (once per Lambda), k_oz_xprep, or k_oz_xprep_sum where every
+// bond carries the same J(t) (gather + scale + slice of X per residual), k_oz_gemm
+// (persistent: TMA + tcgen05.mma kind::f16 into two
 // accumulator sets + FP64 epilogue of the previous tile).  With five slices the
 // accumulators of diagonals 2..6 are consecutive 48-column blocks and so are the X
 // slices in a stage: A_s X_t for t = 1..6-s is one MMA (N = (6 - s) 48) into the
@@ -246,10 +247,8 @@ __global__ void k_oz_xprep(const double2* __restrict__ G, const double* __restri
 }
 
 // The same where every bond carries the same J(t): the factor sits in the Lambda slices
-// (k_oz_aprep with Jrow), and X = sum_j G_j is summed exactly as 2^-FIX fixed-point
-// integers, with no FP64 arithmetic.  The column scale is a power of two at least four
-// times the largest neighbour value, so the sum of four stays within it; one pass finds
-// it and a second (reading the same columns again, from L1 or L2) converts and sums.
+// (k_oz_aprep with Jrow), and X = sum_j G_j needs only additions, done on the FP64 pipe
+// (which this kernel leaves otherwise idle) while the integer pipe cuts the digits.
 template <int NS>
 __global__ void k_oz_xprep_sum(const double2* __restrict__ G, const int* __restrict__ nbr, int Nr, int Nc, int ncol,
                                __nv_bfloat16* __restrict__ xs, double* __restrict__ tau) {
@@ -268,24 +267,27 @@ __global__ void k_oz_xprep_sum(const double2* __restrict__ G, const int* __restr
     col[q] = G + ((size_t)(has[q] ? j : i) * ncol + n) * Nc;
   }
   constexpr int PER_LANE = 256 / 32;
-  constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
-  unsigned long long mb = 0;
+  double2 x[PER_LANE];
+  unsigned int mb = 0;                                     // high words of |x|: their order is the values' order
 #pragma unroll
   for (int u = 0; u < PER_LANE; ++u) {
     const int z = lane + 32 * u;
-    if (z >= Nc) continue;
+    double xr = 0.0, xi = 0.0;
+    if (z < Nc) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (!has[q]) continue;
-      const double2 g = col[q][z];
-      mb = max(mb, max((unsigned long long)__double_as_longlong(g.x) & ABS,
-                       (unsigned long long)__double_as_longlong(g.y) & ABS));
+      for (int q = 0; q < 4; ++q) {
+        if (!has[q]) continue;
+        const double2 g = col[q][z];
+        xr += g.x;
+        xi += g.y;
+      }
     }
+    x[u] = make_double2(xr, xi);
+    mb = max(mb, max((unsigned int)__double2hiint(xr) & 0x7FFFFFFFu, (unsigned int)__double2hiint(xi) & 0x7FFFFFFFu));
   }
-  for (int o = 16; o > 0; o >>= 1) mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, mb, o));
-  // largest value < 2^(Emx - 1022), so 2^e with e = Emx - 1020 bounds four of them
-  const int Emx = (int)((mb >> 52) & 0x7FF);
-  const int e = Emx == 0 ? 0 : Emx - 1020;
+  for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  const int Emx = (int)((mb >> 20) & 0x7FF);
+  const int e = Emx == 0 ? 0 : Emx - 1022;
   if (lane == 0) tau[w] = __longlong_as_double((long long)(e + 1023) << 52);
   const size_t stride = (size_t)Nr * ncol * N2;
   __nv_bfloat16* dst = xs + w * N2;
@@ -293,16 +295,8 @@ __global__ void k_oz_xprep_sum(const double2* __restrict__ G, const int* __restr
   for (int u = 0; u < PER_LANE; ++u) {
     const int z = lane + 32 * u;
     if (z >= Nc) continue;
-    long long vr = 0, vi = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (!has[q]) continue;
-      const double2 g = col[q][z];
-      vr += fixed_right(g.x, FIX - e);
-      vi += fixed_right(g.y, FIX - e);
-    }
-    write_digits_fast<NS>(vr, dst + z, stride);
-    write_digits_fast<NS>(vi, dst + Nc + z, stride);
+    write_digits_fast<NS>(fixed_right(x[u].x, FIX - e), dst + z, stride);
+    write_digits_fast<NS>(fixed_right(x[u].y, FIX - e), dst + Nc + z, stride);
   }
 }
 
