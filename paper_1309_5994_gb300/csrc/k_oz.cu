@@ -460,6 +460,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int m = mt * BM + q4 * 32 + lane;            // planar row: part m / Nc, contour row z = m % Nc
       const int z = m % Nc, part = m / Nc;
       const double sg = sigma[(size_t)site * N2 + m] * ldexp(1.0, -FIX);   // row scale / fixed-point unit
+      const long long sgb = __double_as_longlong(sg);
       const uint32_t tacc = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(buf * ACC_COLS);
       constexpr int CHUNKS = BN / EPI_CHUNK, PER_HALF = CHUNKS / 2;
       int qcur = (nt * BN + half * PER_HALF * EPI_CHUNK) / gs;
@@ -494,14 +495,18 @@ __global__ void __launch_bounds__(THREADS, 1)
                                 acc_to_fixed<4>(__uint_as_float(r4[j]));
           const int n = n0 + j;
           const double2 gv = G[((size_t)site * ncol + n) * Nc + z];
-          double b = 0.0;
-          if (src_site[n] == site) {                    // B = Lambda_s e_{z'} on the source site
+          // sg tau = 2^es from the exponent fields (both are powers of two), by integer
+          // arithmetic; a scale below the normal range drops terms below ~2^-960
+          const long long pe = sgb + __double_as_longlong(tau[(size_t)site * ncol + n]) - (1023ll << 52);
+          const double sc = pe > (1ll << 52) ? __longlong_as_double(pe) : 0.0;
+          double rv = fma((double)acc, sc, -(part ? gv.y : gv.x));
+          if (__builtin_expect(src_site[n] == site, 0)) {   // B = Lambda_s e_{z'} on the source site
             const double2 lv = lam[((size_t)site * Nc + z) * Nc + src_time[n]];
-            b = part ? lv.y : lv.x;
+            rv += part ? lv.y : lv.x;
           }
-          const double rv = b + (double)acc * (sg * tau[(size_t)site * ncol + n]) - (part ? gv.y : gv.x);
-          r32[((size_t)site * ncol + n) * N2 + m] = (float)rv;
-          float d = fabsf((float)rv);
+          const float rf = (float)rv;
+          r32[((size_t)site * ncol + n) * N2 + m] = rf;
+          float d = fabsf(rf);
           d = (d == d) ? d : __int_as_float(0x7f800000);
           runmax = fmaxf(runmax, d);
         }
