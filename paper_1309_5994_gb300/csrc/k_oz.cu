@@ -138,8 +138,9 @@ __device__ __forceinline__ void write_digits_fast(long long V, __nv_bfloat16* ds
 // the diagonal d = A + 2 exactly: an integer N below 2^24 in units of 2^{-7 d}, moved to
 // the 2^-FIX fixed point by one exact scaling, an exact int32 conversion and a shift.
 // The last accumulator (diagonals >= NACC + 1, rounded in FP32) is scaled by 2^FIX and
-// rounded to the nearest integer in 64 bits (its magnitude stays below 2^-18 for
-// K <= 512), so nothing but the part below 2^-FIX is lost.
+// rounded to the nearest integer; its magnitude stays below 2^-18 for K <= 512 (diagonal
+// 6 sums at most 7 2^12 K 2^-42), so the integer fits in 32 bits, the conversion needs
+// no 64-bit (FP64-pipe) instruction, and nothing but the part below 2^-FIX is lost.
 template <int A>
 __device__ __forceinline__ long long acc_to_fixed(float v) {
   if constexpr (A < NACC - 1) {
@@ -147,7 +148,7 @@ __device__ __forceinline__ long long acc_to_fixed(float v) {
     const int N = __float2int_rn(v * __int_as_float((127 + 7 * d) << 23));   // v * 2^{7 d}, exact
     return (long long)N << (FIX - 7 * d);
   } else {
-    return __float2ll_rn(v * __int_as_float((127 + FIX) << 23));            // v * 2^FIX
+    return (long long)__float2int_rn(v * __int_as_float((127 + FIX) << 23));   // v * 2^FIX: |.| < 2^31
   }
 }
 
