@@ -208,13 +208,14 @@ def test_graph_replayed_series_is_bit_identical(torch_cuda, lib, kw, sources, va
     them (every site a source), and with a graph of 2 sweeps, where the series stops
     inside a replay."""
     p = wl.random_tables(wl.small(**kw), seed=23, rel=0.2)
-    out = {}
+    out, syncs = {}, {}
     for gsw in (0, 16, 2):
         s = _solver(p)
         s.set_sweep_variant(variant)
         s.set_graph_sweeps(gsw)
         got, res = _solve(torch_cuda, s, p, sources, 1, tol=1e-10)
         out[gsw] = (got, res.report["sweeps"], res.report["refinements"], res.report["residual"])
+        syncs[gsw] = res.report["host_syncs"]
         if gsw == 16:
             from paper_1309_5994_gb300 import binding
             for bad in (3, -2, 66):
@@ -224,6 +225,8 @@ def test_graph_replayed_series_is_bit_identical(torch_cuda, lib, kw, sources, va
     for gsw in (16, 2):
         assert np.array_equal(out[gsw][0], out[0][0])
         assert out[gsw][1:] == out[0][1:]
+    # one wait per sweep without graphs, one per replay of 16 with them
+    assert syncs[16] < syncs[0] and syncs[0] >= out[0][1]
 
 
 @pytest.mark.parametrize("case", ["nc64_ragged", "nc256_pair", "nc256_fused"])
