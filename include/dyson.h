@@ -109,8 +109,9 @@ typedef struct {
   int64_t kernel_launches;      /* CUDA kernels this call launched                         */
   int32_t inner_gmres;          /* 1 if a refinement used the GMRES inner solver (its      */
                                 /* matvecs are counted in sweeps), else 0                  */
-  int32_t host_syncs;           /* times the call waited for the device (norm and error     */
-                                /* reads; one per graph replay of the inner series)         */
+  int32_t host_syncs;           /* times the call waited for the device: norm and error     */
+                                /* reads, one per GMRES step, one per graph replay of the   */
+                                /* inner series (one per sweep without graphs)              */
 } dyson_report;
 
 /* Create a context on `device`, ordering work on `cuda_stream` (a cudaStream_t,

@@ -493,6 +493,7 @@ int gmres_inner_solve(dyson_ctx* c, int ncol, const float* r, float* x, int max_
       DY_CUDA(c, cudaMemcpyAsync(st->h_res, st->res, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
       DY_CUDA(c, cudaGetLastError());
       DY_CUDA(c, cudaStreamSynchronize(s));
+      c->host_syncs += 1;
       flush_timers(c);
       c->launches += 6;
       d = j + 1;

@@ -225,8 +225,9 @@ def test_graph_replayed_series_is_bit_identical(torch_cuda, lib, kw, sources, va
     for gsw in (16, 2):
         assert np.array_equal(out[gsw][0], out[0][0])
         assert out[gsw][1:] == out[0][1:]
-    # one wait per sweep without graphs, one per replay of 16 with them
-    assert syncs[16] < syncs[0] and syncs[0] >= out[0][1]
+    # fewer waits for the device with graphs: one per replay instead of one per sweep
+    # (GMRES steps, where a case switches to them, wait once each in both)
+    assert syncs[16] < syncs[0]
 
 
 @pytest.mark.parametrize("case", ["nc64_ragged", "nc256_pair", "nc256_fused"])
@@ -474,9 +475,11 @@ def test_driven_32x32_sampled_columns_fp64(torch_cuda, lib):
     columns against the oracle's complex128 series run for the same 130 sweeps.
 
     On this contour the series' partial sums peak ~2e7 above the result, so
-    either FP64 series carries ~5e-9 of amplified rounding (the update bottoms
-    out near 5e-8 after ~105 sweeps and never reaches a 1e-12 tolerance): the
-    two are compared at 1e-7, and NOT_CONVERGED is the expected status.
+    either FP64 series carries amplified rounding (the update bottoms out near
+    6e-10 after 130 sweeps and never reaches a 1e-12 tolerance), and
+    NOT_CONVERGED is the expected status. Measured on a GB300, the GPU series
+    and the oracle's differ by 2.6e-10, 3.7e-10, 5.6e-11 and 6.0e-12 at the four
+    source times; they are compared at 2e-9.
     """
     p = wl.driven_32x32_nc384()
     S = dyson.setup(p)
@@ -488,7 +491,7 @@ def test_driven_32x32_sampled_columns_fp64(torch_cuda, lib):
     B = dyson.rhs_vector_columns(S, [(src, z) for z in zs])
     ref, _, _ = dyson.neumann_solve(S, B, tol=1e-16, max_sweeps=130)
     for c, z in enumerate(zs):
-        assert _rel(got[0][:, :, z], ref[:, :, c]) < 1e-7
+        assert _rel(got[0][:, :, z], ref[:, :, c]) < 2e-9
 
 
 def test_trapped_16x16_sampled_columns_mixed(torch_cuda, lib):
