@@ -520,21 +520,24 @@ def test_trapped_16x16_sampled_columns_mixed(torch_cuda, lib):
 
 def test_trapped_16x16_bench_launch_shape_sampled_columns(torch_cuda, lib):
     """The benchmark's launch configuration on its workload: 16 block columns of the 16x16,
-    Nc = 256 lattice in one chunk (single-CTA sweep variant, support truncation on, as the
-    tuner picks), mixed precision at the benchmark's tolerance 1e-6, sources 112..127 (one
-    of its batches).  Sampled vector columns of four block columns, and the densities of two
+    Nc = 256 lattice in one chunk (the fused sweep on CTA pairs, as the tuner picks, support
+    truncation on, the inner series from replayed graphs of 16 sweeps), mixed precision at
+    the benchmark's tolerance 1e-6, sources 112..127 (one of its batches).  Sampled vector columns of four block columns, and the densities of two
     sources at three times, against the oracle's complex128 series; bound 1e-6 relative."""
     torch = torch_cuda
     from paper_1309_5994_gb300 import binding
     p = wl.trapped_16x16_nc256()
     S = dyson.setup(p)
     s = _solver(p)
-    s.set_sweep_variant(binding.SWEEP_SINGLE_CTA)
+    s.set_sweep_variant(binding.SWEEP_FUSED_PAIR)
     s.set_chunk(16)
+    s.profile(True)
     sources = list(range(112, 128))
     g = torch.empty((len(sources), p.Nr, p.Nc, p.Nc), dtype=torch.complex128, device="cuda:0")
     res = s.solve(sources, precision=binding.PREC_TF32X3_F64REF, tol=1e-6, max_sweeps=400, g_out=g)
     assert res.report["chunks"] == 1
+    assert s.profile_query(binding.KERNEL_SWEEP_TC_FUSED)[0] > 0          # the fused sweep ran
+    assert res.report["host_syncs"] < res.report["sweeps"]                 # from replayed graphs
     rng = np.random.default_rng(11)
     picks = [(q, int(z)) for q in (0, 5, 10, 15) for z in rng.choice(p.Nc, 2, replace=False)]
     dens = [(q, z) for q in (0, 7) for z in (0, p.Nt // 2, p.Nt - 1)]
